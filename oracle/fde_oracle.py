@@ -1,0 +1,549 @@
+"""Plain FP64 oracle: definitions of the FDE systems, the tau preconditioner
+P_F and textbook PCG / GMRES(m).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Section numbers refer to
+the paper "Preconditioners for Fractional Diffusion Equations Based on the
+Spectral Symbol":
+
+  Sec. 1.2  shifted Grunwald weights g_k, Toeplitz T_{alpha,n}, the 1D system
+            (nu I + D_+ T + D_- T^T) u = nu u_prev + h^alpha f, nu = h^alpha/h_t
+  Sec. 1.3  WSGD weights w_k and S_{alpha,n}
+  Sec. 1.4  2D system, x-fastest ordering, A_x, A_y, Crank-Nicolson form
+  Sec. 2.1  symbols g_alpha(theta), w_alpha(theta)
+  Sec. 2.2  Theorem 2: p_alpha = g_alpha(theta)+g_alpha(-theta),
+            q_alpha = w_alpha(theta)+w_alpha(-theta)
+  Sec. 1    (introduction) tau_n(f) = S diag(f(theta)) S, theta_j = j pi/(n+1),
+            [S]_ij = sqrt(2/(n+1)) sin(i theta_j)
+  Sec. 3.1  P_F = D_n tau_n(p_alpha), D_n = (D_+ + D_-)/2
+  Sec. 3.1.1 Case I: shifted symbol p_alpha + 2 nu/(d_+ + d_-)
+  Sec. 3.2  2D: P = D_N (S (x) S) F_N (S (x) S), D_N = (D_+ + D_- + E_+ + E_-)/4,
+            F = q_alpha(theta_1) + (s/r) q_beta(theta_2); shifted P_hat with
+            1/r + d q_alpha + (s/r) e q_beta and no D
+  Sec. 4    GMRES with tolerance 1e-7; Examples 1-3, Tables 1-4
+
+Readings of the paper that are not fixed by its text (each also listed in the
+design notes):
+  * ORDER_TAU_D: the tabulated condition numbers of Tables 1-4 are reproduced
+    by P = tau(F) D (P^-1 = D^-1 tau^-1); the formula in Sec. 3.1 / 3.2 writes
+    P = D tau(F).  Both orders are provided; tau_D is the default.
+  * 2D implicit Euler (used by the workloads) is
+    (nu I + A_x + (h_x^alpha/h_y^beta) A_y) u = nu u_prev + h_x^alpha f.
+  * Iteration count = number of products with M after the initial residual.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+
+__all__ = [
+    "grunwald_weights", "wsgd_weights", "scheme_weights", "toeplitz_from_weights",
+    "symbol_g", "symbol_w", "symbol_p", "symbol_q", "scheme_symbol", "tau_grid",
+    "sine_matrix", "tau_matrix", "Problem1D", "Problem2D", "Tau1D", "Tau2D",
+    "pcg", "gmres", "KrylovResult", "preconditioned_condition_number",
+    "apply_sine_fast", "ORDER_TAU_D", "ORDER_D_TAU", "GL1", "WSGD2",
+]
+
+GL1 = "gl1"      # first-order shifted Grunwald weights g_k (Sec. 1.2)
+WSGD2 = "wsgd2"  # second-order weighted-and-shifted weights w_k (Sec. 1.3)
+ORDER_TAU_D = "tau_d"   # P = tau(F) D   (reproduces Tables 1-4)
+ORDER_D_TAU = "d_tau"   # P = D tau(F)   (as printed in Sec. 3.1 / 3.2)
+
+
+# ----------------------------------------------------------------------------
+# Weights and Toeplitz matrices (Sec. 1.2, 1.3)
+# ----------------------------------------------------------------------------
+
+def grunwald_weights(alpha: float, K: int) -> np.ndarray:
+    """g_k = (-1)^k binom(alpha, k), k = 0..K (Sec. 1.2).
+
+    Evaluated as the product (-1)^k/k! * alpha(alpha-1)...(alpha-k+1) written as
+    a running product: each factor multiplies by -(alpha-k+1)/k.
+    """
+    g = np.empty(K + 1, dtype=np.float64)
+    g[0] = 1.0
+    for k in range(1, K + 1):
+        g[k] = g[k - 1] * (-(alpha - k + 1.0) / k)
+    return g
+
+
+def wsgd_weights(alpha: float, K: int) -> np.ndarray:
+    """w_0 = (alpha/2) g_0, w_k = (alpha/2) g_k + ((2-alpha)/2) g_{k-1} (Sec. 1.3)."""
+    g = grunwald_weights(alpha, K)
+    w = np.empty_like(g)
+    w[0] = 0.5 * alpha * g[0]
+    w[1:] = 0.5 * alpha * g[1:] + 0.5 * (2.0 - alpha) * g[:-1]
+    return w
+
+
+def scheme_weights(alpha: float, K: int, scheme: str) -> np.ndarray:
+    if scheme == GL1:
+        return grunwald_weights(alpha, K)
+    if scheme == WSGD2:
+        return wsgd_weights(alpha, K)
+    raise ValueError(f"unknown scheme {scheme!r}")
+
+
+def toeplitz_from_weights(wts: np.ndarray, n: int) -> np.ndarray:
+    """T = -[w_{i-j+1}] for i-j+1 >= 0, zero above the first superdiagonal
+    (eq. for T_{alpha,n} in Sec. 1.2; S_{alpha,n} in Sec. 1.3 with w_k).
+
+    Built entry by entry from the weights.
+    """
+    if len(wts) < n + 1:
+        raise ValueError("need weights w_0..w_n")
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    k = i - j + 1                       # weight index of entry (i, j)
+    return np.where(k >= 0, -np.asarray(wts, dtype=np.float64)[np.clip(k, 0, n)], 0.0)
+
+
+# ----------------------------------------------------------------------------
+# Symbols (Sec. 2.1, 2.2) and the tau algebra (Sec. 1)
+# ----------------------------------------------------------------------------
+
+def symbol_g(alpha: float, theta) -> np.ndarray:
+    """g_alpha(theta) = -e^{-i theta} (1 - e^{i theta})^alpha (Sec. 2.1),
+    principal branch of the complex power."""
+    theta = np.asarray(theta, dtype=np.float64)
+    z = 1.0 - np.exp(1j * theta)
+    return -np.exp(-1j * theta) * np.power(z, alpha)
+
+
+def symbol_w(alpha: float, theta) -> np.ndarray:
+    """w_alpha(theta) = -((2 - alpha(1 - e^{-i theta}))/2)(1 - e^{i theta})^alpha
+    (Sec. 2.1, symbol of S_{alpha,n})."""
+    theta = np.asarray(theta, dtype=np.float64)
+    c = (2.0 - alpha * (1.0 - np.exp(-1j * theta))) / 2.0
+    return -c * np.power(1.0 - np.exp(1j * theta), alpha)
+
+
+def symbol_p(alpha: float, theta) -> np.ndarray:
+    """p_alpha(theta) = g_alpha(theta) + g_alpha(-theta) (Theorem 2). Real."""
+    v = symbol_g(alpha, theta) + symbol_g(alpha, -np.asarray(theta, dtype=np.float64))
+    return np.real(v)
+
+
+def symbol_q(alpha: float, theta) -> np.ndarray:
+    """q_alpha(theta) = w_alpha(theta) + w_alpha(-theta) (Theorem 2). Real."""
+    v = symbol_w(alpha, theta) + symbol_w(alpha, -np.asarray(theta, dtype=np.float64))
+    return np.real(v)
+
+
+def scheme_symbol(alpha: float, theta, scheme: str) -> np.ndarray:
+    """F_alpha: p_alpha for the first-order scheme, q_alpha for WSGD (Thm 2)."""
+    return symbol_p(alpha, theta) if scheme == GL1 else symbol_q(alpha, theta)
+
+
+def tau_grid(n: int) -> np.ndarray:
+    """theta_j = j pi/(n+1), j = 1..n (Sec. 1)."""
+    return np.arange(1, n + 1, dtype=np.float64) * (np.pi / (n + 1))
+
+
+def sine_matrix(n: int) -> np.ndarray:
+    """[S_n]_{ij} = sqrt(2/(n+1)) sin(i theta_j), i,j = 1..n (Sec. 1)."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return math.sqrt(2.0 / (n + 1)) * np.sin(np.outer(i, i) * (np.pi / (n + 1)))
+
+
+def tau_matrix(f_samples: np.ndarray) -> np.ndarray:
+    """tau_n(f) = S diag(f(theta)) S (Sec. 1)."""
+    S = sine_matrix(len(f_samples))
+    return S @ np.diag(f_samples) @ S
+
+
+def apply_sine_fast(v: np.ndarray, axis: int = -1) -> np.ndarray:
+    """S_n applied along one axis through the library DST-I (orthonormal type 1),
+    which computes the same sum sqrt(2/(n+1)) sum_k v_k sin(j k pi/(n+1)).
+
+    Used only at sizes where the explicit dense S would not fit; the tests pin
+    it to ``sine_matrix``.
+    """
+    import scipy.fft
+    return scipy.fft.dst(v, type=1, norm="ortho", axis=axis)
+
+
+# ----------------------------------------------------------------------------
+# Problems
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Problem1D:
+    """M = c0 I + D_+ T + D_- T^T (Sec. 1.2), T from ``scheme`` weights.
+
+    c0 is nu = h^alpha / h_t for implicit Euler.
+    """
+    alpha: float
+    n: int
+    c0: float
+    dp: np.ndarray
+    dm: np.ndarray
+    scheme: str = GL1
+    _T: Optional[np.ndarray] = field(default=None, repr=False)
+    _w: Optional[np.ndarray] = field(default=None, repr=False)
+
+    @property
+    def N(self) -> int:
+        return self.n
+
+    def weights(self) -> np.ndarray:
+        if self._w is None:
+            self._w = scheme_weights(self.alpha, self.n + 1, self.scheme)
+        return self._w
+
+    def T(self) -> np.ndarray:
+        if self._T is None:
+            self._T = toeplitz_from_weights(self.weights(), self.n)
+        return self._T
+
+    def dense(self) -> np.ndarray:
+        T = self.T()
+        return self.c0 * np.eye(self.n) + self.dp[:, None] * T + self.dm[:, None] * T.T
+
+    def matvec(self, x: np.ndarray, method: str = "auto") -> np.ndarray:
+        """y = c0 x + d_+ (T x) + d_- (T^T x).
+
+        method="dense" (default up to n = 4096): the dense T.  method="direct":
+        the same Toeplitz sums evaluated by direct (non-FFT) convolution of the
+        weight sequence with x, (T x)_i = -sum_j w_{i-j+1} x_j.
+        """
+        x = np.asarray(x, dtype=np.float64)
+        n = self.n
+        if method == "dense" or (method == "auto" and n <= 4096):
+            T = self.T()
+            return self.c0 * x + self.dp * (T @ x) + self.dm * (T.T @ x)
+        w = self.weights()
+        full = np.convolve(w, x)                 # full[k] = sum_j w[k-j] x_j
+        Tx = -full[1:n + 1]                      # k = i + 1
+        fullr = np.convolve(w, x[::-1])          # (T^T x)_i = -sum_j w[j-i+1] x_j
+        Ttx = -fullr[n - np.arange(n)]
+        return self.c0 * x + self.dp * Tx + self.dm * Ttx
+
+    def matvec_rows(self, x: np.ndarray, rows: np.ndarray) -> np.ndarray:
+        """Selected entries y_i of M x, each from its row of the definition."""
+        x = np.asarray(x, dtype=np.float64)
+        w = self.weights()
+        n = self.n
+        out = np.empty(len(rows))
+        for t, i in enumerate(rows):
+            j = np.arange(0, min(i + 2, n))
+            tx = -np.dot(w[i - j + 1], x[j])
+            j2 = np.arange(max(i - 1, 0), n)
+            ttx = -np.dot(w[j2 - i + 1], x[j2])
+            out[t] = self.c0 * x[i] + self.dp[i] * tx + self.dm[i] * ttx
+        return out
+
+
+@dataclass
+class Problem2D:
+    """M = c0 I + D_+(I (x) S_a) + D_-(I (x) S_a^T) + sr (E_+(S_b (x) I) + E_-(S_b^T (x) I))
+    (Sec. 1.4 and eq. for M_(alpha,beta),N in Sec. 3.2), x-fastest ordering:
+    u[i + j*n1] = u(x_i, y_j); coefficient arrays have shape (n2, n1).
+
+    c0 = 1/r and sr = s/r for Crank-Nicolson; c0 = nu, sr = h_x^alpha/h_y^beta
+    for implicit Euler.
+    """
+    alpha: float
+    beta: float
+    n1: int
+    n2: int
+    c0: float
+    sr: float
+    dp: np.ndarray
+    dm: np.ndarray
+    ep: np.ndarray
+    em: np.ndarray
+    scheme: str = WSGD2
+    _Ta: Optional[np.ndarray] = field(default=None, repr=False)
+    _Tb: Optional[np.ndarray] = field(default=None, repr=False)
+
+    @property
+    def N(self) -> int:
+        return self.n1 * self.n2
+
+    def Ta(self) -> np.ndarray:
+        if self._Ta is None:
+            self._Ta = toeplitz_from_weights(scheme_weights(self.alpha, self.n1 + 1, self.scheme), self.n1)
+        return self._Ta
+
+    def Tb(self) -> np.ndarray:
+        if self._Tb is None:
+            self._Tb = toeplitz_from_weights(scheme_weights(self.beta, self.n2 + 1, self.scheme), self.n2)
+        return self._Tb
+
+    def dense(self) -> np.ndarray:
+        """Explicit Kronecker-product matrix (small N only)."""
+        I1, I2 = np.eye(self.n1), np.eye(self.n2)
+        Ta, Tb = self.Ta(), self.Tb()
+        Ax = self.dp.reshape(-1)[:, None] * np.kron(I2, Ta) + self.dm.reshape(-1)[:, None] * np.kron(I2, Ta.T)
+        Ay = self.ep.reshape(-1)[:, None] * np.kron(Tb, I1) + self.em.reshape(-1)[:, None] * np.kron(Tb.T, I1)
+        return self.c0 * np.eye(self.N) + Ax + self.sr * Ay
+
+    def matvec(self, x: np.ndarray) -> np.ndarray:
+        """The Kronecker products applied as matrix products on the (n2, n1)
+        grid: (I (x) A) u <-> U A^T, (B (x) I) u <-> B U."""
+        U = np.asarray(x, dtype=np.float64).reshape(self.n2, self.n1)
+        Ta, Tb = self.Ta(), self.Tb()
+        Y = (self.c0 * U + self.dp * (U @ Ta.T) + self.dm * (U @ Ta)
+             + self.sr * (self.ep * (Tb @ U) + self.em * (Tb.T @ U)))
+        return Y.reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# tau preconditioners (Sec. 3.1, 3.2)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Tau1D:
+    """P = D tau(F) (ORDER_D_TAU) or tau(F) D (ORDER_TAU_D), tau(F) = S diag(F) S.
+
+    D = None means D = I.
+    """
+    F: np.ndarray
+    D: Optional[np.ndarray] = None
+    order: str = ORDER_TAU_D
+
+    @staticmethod
+    def for_problem(prob: Problem1D, shift: bool = False, order: str = ORDER_TAU_D) -> "Tau1D":
+        """P_F of Sec. 3.1: F = F_alpha(theta_j), D_n = (D_+ + D_-)/2.
+
+        shift=True is Case I (Sec. 3.1.1, constant d_+, d_-): the symbol becomes
+        F_alpha + 2 nu/(d_+ + d_-).
+        """
+        F = scheme_symbol(prob.alpha, tau_grid(prob.n), prob.scheme)
+        D = 0.5 * (prob.dp + prob.dm)
+        if shift:
+            dsum = prob.dp + prob.dm
+            if not np.all(dsum == dsum[0]):
+                raise ValueError("the Case I shift needs constant coefficients")
+            F = F + 2.0 * prob.c0 / dsum[0]
+        return Tau1D(F=F, D=D, order=order)
+
+    def tau_inv(self, r: np.ndarray) -> np.ndarray:
+        n = len(self.F)
+        if n <= 4096:
+            S = sine_matrix(n)
+            return S @ ((S @ r) / self.F)
+        return apply_sine_fast(apply_sine_fast(r) / self.F)
+
+    def apply_inverse(self, r: np.ndarray) -> np.ndarray:
+        r = np.asarray(r, dtype=np.float64)
+        if self.D is None:
+            return self.tau_inv(r)
+        if self.order == ORDER_TAU_D:      # P^-1 = D^-1 tau^-1
+            return self.tau_inv(r) / self.D
+        return self.tau_inv(r / self.D)    # P^-1 = tau^-1 D^-1
+
+    def dense(self) -> np.ndarray:
+        tau = tau_matrix(self.F)
+        if self.D is None:
+            return tau
+        if self.order == ORDER_TAU_D:
+            return tau * self.D[None, :]
+        return self.D[:, None] * tau
+
+
+@dataclass
+class Tau2D:
+    """P = D_N (S2 (x) S1) F_N (S2 (x) S1) (ORDER_D_TAU) or with D_N on the right
+    (ORDER_TAU_D); F_N[j, i] = F(theta_{1,i}, theta_{2,j}) on the (n2, n1) grid."""
+    F: np.ndarray            # shape (n2, n1)
+    D: Optional[np.ndarray] = None
+    order: str = ORDER_TAU_D
+
+    @staticmethod
+    def for_problem(prob: Problem2D, shift: bool = False, order: str = ORDER_TAU_D) -> "Tau2D":
+        """Sec. 3.2.  shift=False: F = F_a(theta_1) + sr F_b(theta_2) with
+        D_N = (D_+ + D_- + E_+ + E_-)/4.  shift=True (P_hat, constant d, e):
+        F = c0 + d F_a(theta_1) + sr e F_b(theta_2), no D."""
+        fa = scheme_symbol(prob.alpha, tau_grid(prob.n1), prob.scheme)
+        fb = scheme_symbol(prob.beta, tau_grid(prob.n2), prob.scheme)
+        if shift:
+            d = prob.dp.reshape(-1)[0]
+            e = prob.ep.reshape(-1)[0]
+            for arr, v in ((prob.dp, d), (prob.dm, d), (prob.ep, e), (prob.em, e)):
+                if not np.all(arr == v):
+                    raise ValueError("P_hat needs d_+ = d_- = d and e_+ = e_- = e constant")
+            F = prob.c0 + d * fa[None, :] + prob.sr * e * fb[:, None]
+            return Tau2D(F=F, D=None, order=order)
+        F = fa[None, :] + prob.sr * fb[:, None]
+        D = 0.25 * (prob.dp + prob.dm + prob.ep + prob.em)
+        return Tau2D(F=F, D=D, order=order)
+
+    def tau_inv(self, r: np.ndarray) -> np.ndarray:
+        n2, n1 = self.F.shape
+        R = np.asarray(r, dtype=np.float64).reshape(n2, n1)
+        if max(n1, n2) <= 4096:
+            S1, S2 = sine_matrix(n1), sine_matrix(n2)
+            Z = S2 @ ((S2 @ R @ S1) / self.F) @ S1
+        else:
+            t = apply_sine_fast(apply_sine_fast(R, axis=1), axis=0)
+            Z = apply_sine_fast(apply_sine_fast(t / self.F, axis=0), axis=1)
+        return Z.reshape(-1)
+
+    def apply_inverse(self, r: np.ndarray) -> np.ndarray:
+        r = np.asarray(r, dtype=np.float64)
+        if self.D is None:
+            return self.tau_inv(r)
+        D = self.D.reshape(-1)
+        if self.order == ORDER_TAU_D:
+            return self.tau_inv(r) / D
+        return self.tau_inv(r / D)
+
+    def dense(self) -> np.ndarray:
+        n2, n1 = self.F.shape
+        SS = np.kron(sine_matrix(n2), sine_matrix(n1))
+        tau = SS @ np.diag(self.F.reshape(-1)) @ SS
+        if self.D is None:
+            return tau
+        D = self.D.reshape(-1)
+        if self.order == ORDER_TAU_D:
+            return tau * D[None, :]
+        return D[:, None] * tau
+
+
+def preconditioned_condition_number(M: np.ndarray, P: np.ndarray) -> float:
+    """kappa_2(P^-1 M), as tabulated in Tables 1-4."""
+    return float(np.linalg.cond(np.linalg.solve(P, M)))
+
+
+# ----------------------------------------------------------------------------
+# Krylov solvers (textbook)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class KrylovResult:
+    x: np.ndarray
+    iterations: int
+    converged: bool
+    relres: float                 # true ||b - M x|| / ||b||
+    restarts: int = 0
+    history: list = field(default_factory=list)
+
+
+def pcg(A: Callable, b: np.ndarray, Pinv: Optional[Callable] = None, x0=None,
+        tol: float = 1e-8, maxiter: int = 10000) -> KrylovResult:
+    """Preconditioned conjugate gradients (Hestenes-Stiefel).
+
+    Stops when ||r_k||_2 <= tol ||b||_2; the iteration count is the number of
+    products with A after the initial residual.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    Pinv = Pinv or (lambda v: v.copy())
+    nb = np.linalg.norm(b)
+    r = b - A(x)
+    hist = [np.linalg.norm(r) / nb]
+    its = 0
+    if hist[-1] <= tol:
+        return KrylovResult(x, 0, True, hist[-1], history=hist)
+    z = Pinv(r)
+    p = z.copy()
+    rz = float(r @ z)
+    converged = False
+    while its < maxiter:
+        q = A(p)
+        its += 1
+        a = rz / float(p @ q)
+        x += a * p
+        r -= a * q
+        hist.append(np.linalg.norm(r) / nb)
+        if hist[-1] <= tol:
+            converged = True
+            break
+        z = Pinv(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    relres = float(np.linalg.norm(b - A(x)) / nb)
+    return KrylovResult(x, its, converged, relres, history=hist)
+
+
+def gmres(A: Callable, b: np.ndarray, Pinv: Optional[Callable] = None, x0=None,
+          side: str = "right", restart: int = 30, tol: float = 1e-8,
+          maxiter: int = 10000) -> KrylovResult:
+    """Restarted GMRES(m) with modified Gram-Schmidt Arnoldi and Givens rotations.
+
+    side="right": Krylov space of A P^-1; stops when the Arnoldi residual
+    estimate |g_{j+1}| <= tol ||b|| (the true residual norm in exact arithmetic).
+    side="left": Krylov space of P^-1 A; stops when ||P^-1 (b - A x)|| <=
+    tol ||P^-1 (b - A x0)||, the convention the paper's experiments (Sec. 4)
+    are reproduced with.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    n = len(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    Pinv = Pinv or (lambda v: v.copy())
+    nb = np.linalg.norm(b)
+    m = restart
+    its = 0
+    restarts = 0
+    hist = []
+
+    def residual(xv):
+        r = b - A(xv)
+        return Pinv(r) if side == "left" else r
+
+    r = residual(x)
+    beta = np.linalg.norm(r)
+    ref = beta if side == "left" else nb
+    hist.append(beta / ref if ref > 0 else 0.0)
+    if beta <= tol * ref:
+        return KrylovResult(x, 0, True, float(np.linalg.norm(b - A(x)) / nb), 0, hist)
+    converged = False
+    while its < maxiter:
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(m):
+            if side == "right":
+                w = A(Pinv(V[j]))
+            else:
+                w = Pinv(A(V[j]))
+            its += 1
+            for i in range(j + 1):
+                H[i, j] = float(w @ V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            breakdown = H[j + 1, j] == 0.0
+            if not breakdown:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = math.hypot(H[j, j], H[j + 1, j])
+            cs[j] = H[j, j] / den
+            sn[j] = H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            hist.append(abs(g[j + 1]) / ref)
+            if abs(g[j + 1]) <= tol * ref or breakdown or its >= maxiter:
+                converged = abs(g[j + 1]) <= tol * ref or breakdown
+                break
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        u = V[:k].T @ y
+        x += Pinv(u) if side == "right" else u
+        if converged or its >= maxiter:
+            break
+        restarts += 1
+        r = residual(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * ref:
+            converged = True
+            break
+    relres = float(np.linalg.norm(b - A(x)) / nb)
+    return KrylovResult(x, its, converged, relres, restarts, hist)
