@@ -1,0 +1,177 @@
+/*
+ * fde.h — C ABI of libfde: symbol-based tau-preconditioned Krylov solves of
+ * shifted-Grunwald fractional diffusion systems on one GB300 (sm_103a).
+ *
+ * Method: Barakitis, Ekstrom, Vassalos, "Preconditioners for Fractional
+ * Diffusion Equations Based on the Spectral Symbol".
+ *
+ *   1D (Sec. 1.2, eq. for M_{alpha,n}):  M = c0 I + D_+ T + D_- T^T,
+ *       T = T_{alpha,n} = -[g_{i-j+1}] (first-order weights g_k = (-1)^k binom(alpha,k))
+ *       or S_{alpha,n} = -[w_{i-j+1}] (second-order WSGD weights, Sec. 1.3);
+ *       c0 = nu = h^alpha / dt for implicit Euler.
+ *   2D (Sec. 1.4 and Sec. 3.2):  M = c0 I + D_+(I (x) T_a) + D_-(I (x) T_a^T)
+ *                                 + sr [E_+(T_b (x) I) + E_-(T_b^T (x) I)],
+ *       x-fastest ordering u[i + j*n1]; implicit Euler c0 = h_x^alpha/dt,
+ *       sr = h_x^alpha / h_y^beta (Crank-Nicolson: c0 = 1/r = 2 h_x^alpha/dt, same sr).
+ *   Preconditioner (Sec. 3.1 eq. P_F, Sec. 3.2 eq. for the 2D P):
+ *       P = D tau(F) or tau(F) D, tau(F) = S diag(F(theta)) S (DST-I, Sec. 1),
+ *       F = F_alpha (1D) or F_a(theta_1) + sr F_b(theta_2) (2D), D = mean of the
+ *       diffusion coefficients; with tau_shift the constant-coefficient shifted
+ *       symbols of Sec. 3.1.1 (Case I) and Sec. 3.2 (P_hat, no D).
+ *
+ * Conventions for every entry point:
+ *   - All vector arguments are DEVICE pointers (cudaMalloc / torch CUDA memory)
+ *     unless stated; the caller owns them and the workspace.  The library
+ *     owns only the small host-side plan struct.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*,
+ *     NULL = legacy default stream); no call allocates device memory or
+ *     synchronises the host, except fde_assemble_symbol's one-time kernel
+ *     attribute setup on first use.
+ *   - Arguments are validated before any launch; invalid input returns
+ *     FDE_EINVAL and launches nothing.  A failed launch returns FDE_ECUDA.
+ *     Convergence failures are reported per solve in fde_solve_info (device
+ *     memory), never by aborting; no C++ exception crosses the ABI.
+ *   - Grid sizes: n1 + 1 (and n2 + 1 in 2D) must be powers of two, 1 <= n+1.
+ */
+#ifndef FDE_H
+#define FDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FDE_OK = 0,
+    FDE_EINVAL = 1,        /* invalid argument (checked before any launch) */
+    FDE_ENOMEM = 2,        /* workspace smaller than fde_workspace_size() */
+    FDE_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+    FDE_ENOCONV = 4,       /* iteration cap reached; best iterate left in x */
+    FDE_EBREAKDOWN = 5,    /* PCG p^T A p <= 0, or a non-positive preconditioner */
+    FDE_ETIMEOUT = 6,      /* an inter-CTA barrier wait exceeded its bound */
+    FDE_ENONFINITE = 7     /* NaN/Inf met in a reduction */
+} fde_status;
+
+typedef enum { FDE_F64 = 0, FDE_F32 = 1 } fde_dtype;
+typedef enum { FDE_WEIGHTS_GL1 = 0, FDE_WEIGHTS_WSGD2 = 1 } fde_weights;
+typedef enum { FDE_ORDER_TAU_D = 0, FDE_ORDER_D_TAU = 1 } fde_order;
+typedef enum { FDE_SCHEME_IMPLICIT_EULER = 0, FDE_SCHEME_CRANK_NICOLSON = 1 } fde_scheme;
+typedef enum { FDE_PCG = 0, FDE_GMRES = 1 } fde_method;
+typedef enum {
+    FDE_PREC_F64 = 0,      /* every vector, transform and reduction in FP64 */
+    FDE_PREC_F32 = 1,      /* FP32 vectors and transforms; FP64 dots and scalars; no refinement */
+    FDE_PREC_F32_IR = 2    /* FP32 inner solves, FP64 outer residual r = b - A x and update */
+} fde_precision;
+typedef enum { FDE_SIDE_RIGHT = 0, FDE_SIDE_LEFT = 1 } fde_side;
+
+/*
+ * The problem of one time step, in the paper's terms (Sec. 1.2-1.4).
+ * Coefficient arrays: device FP64, length n1*n2, x fastest; a NULL array means
+ * the matching *_const scalar is used everywhere.
+ */
+typedef struct {
+    int dim;               /* 1 or 2 */
+    int n1, n2;            /* interior points per axis (n2 ignored in 1D); n+1 = 2^k */
+    double alpha, beta;    /* fractional orders in (1,2); beta ignored in 1D */
+    double len1, len2;     /* domain lengths R-L, so h = len/(n+1) */
+    double dt;             /* time step h_t > 0 */
+    int scheme;            /* fde_scheme: sets c0 = h^alpha/dt or 2 h^alpha/dt */
+    int weights;           /* fde_weights */
+    const double *dp, *dm, *ep, *em;        /* d_+, d_-, e_+, e_- (device) or NULL */
+    double dp_const, dm_const, ep_const, em_const;
+    int tau_shift;         /* 1: shifted symbol (needs constant, equal coefficients) */
+    int order;             /* fde_order: P = tau(F) D (default) or D tau(F) */
+} fde_problem;
+
+typedef struct {
+    int method;            /* fde_method */
+    int restart;           /* GMRES(m) restart length m, 1..64 */
+    double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2 (right precond.) */
+    int max_iters;         /* cap on products with M (inner iterations), >= 1 */
+    int precision;         /* fde_precision */
+    double inner_tol;      /* FDE_PREC_F32_IR: relative tolerance of each inner solve */
+    int max_outer;         /* FDE_PREC_F32_IR: cap on refinement steps */
+    int side;              /* fde_side (GMRES only; PCG ignores it) */
+} fde_solve_opts;
+
+/* Per-solve result, written by the device into caller memory. */
+typedef struct {
+    int32_t status;        /* fde_status */
+    int32_t iterations;    /* products with M inside the Krylov loops (inner, all restarts) */
+    int32_t outer;         /* refinement steps (FDE_PREC_F32_IR), else 0 */
+    int32_t restarts;      /* GMRES restarts */
+    double relres;         /* final true ||b - A x||_2/||b||_2, FP64 */
+    double relres_est;     /* the Krylov loop's own last residual estimate */
+} fde_solve_info;
+
+typedef struct fde_plan fde_plan;
+
+/* Default options: GMRES(30), tol 1e-8, 5000 iterations, FP64, right side. */
+void fde_default_opts(fde_solve_opts* opts);
+
+/*
+ * Bytes of device workspace that a plan for (prob, opts) needs: symbol data
+ * (circulant eigenvalues of T, tau samples, twiddles, D^{-1}), Krylov vectors
+ * and transform intermediates.  Host-only; touches no device memory.
+ * Returns FDE_EINVAL for an invalid problem or options.
+ */
+fde_status fde_workspace_size(const fde_problem* prob, const fde_solve_opts* opts, size_t* bytes);
+
+/*
+ * Assemble the symbol data of `prob` into `workspace` (device, >= bytes from
+ * fde_workspace_size, 256-byte aligned) on `stream` and return a host plan.
+ * Computes on the device, in FP64: the weights g_k or w_k (Sec. 1.2/1.3), the
+ * eigenvalues of the 2(n+1)-circulant that embeds T (FFT of its first
+ * column), the tau samples F(theta_j) (Thm 2; shifted per Sec. 3.1.1 / 3.2),
+ * D^{-1}, and FP32 copies of all of them.  The coefficient arrays in `prob`
+ * must stay valid for the plan's lifetime.  `opts` fixes the solver
+ * workspace layout; later solves must use the same method/precision/restart.
+ */
+fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* opts,
+                               void* workspace, size_t bytes, fde_plan** plan, void* stream);
+
+/*
+ * y = M x (Sec. 1.2 eq. for M_{alpha,n}; Sec. 3.2 eq. for M_(alpha,beta),N):
+ * the Toeplitz products by circulant embedding and FFT, with c0, D_+-, E_+-
+ * and sr fused.  x, y: device arrays of n1*n2 elements of `dtype`; x != y.
+ */
+fde_status fde_toeplitz_matvec(const fde_plan* plan, int dtype, const void* x, void* y, void* stream);
+
+/*
+ * z = P^{-1} r (Sec. 3.1 eq. P_F; Sec. 3.2): DST-I, division by the symbol
+ * samples, DST-I (per axis in 2D), with D^{-1} before or after per `order`.
+ * r, z: device arrays of n1*n2 elements of `dtype`; r != z.
+ */
+fde_status fde_tau_solve(const fde_plan* plan, int dtype, const void* r, void* z, void* stream);
+
+/*
+ * Solve M_i x_i = b_i for count >= 1 independent plans in ONE persistent
+ * cooperative launch.  b[i], x[i]: device FP64 arrays; x[i] holds the initial
+ * guess on entry and the solution on exit.  `b` and `x` are HOST arrays of
+ * device pointers.  info_dev: device array of `count` fde_solve_info.
+ * All plans must have been assembled with the same opts->method/precision and
+ * restart; opts->tol/max_iters/inner_tol/max_outer may differ from assembly.
+ */
+fde_status fde_krylov_solve(const fde_plan* const* plans, int count, const double* const* b,
+                            double* const* x, const fde_solve_opts* opts,
+                            fde_solve_info* info_dev, void* stream);
+
+/*
+ * Right-hand side of one implicit-Euler step (Sec. 1.2): b = c0 u_prev + h^alpha f.
+ * f may be NULL (f = 0).  Device FP64 arrays of n1*n2 elements.
+ */
+fde_status fde_step_rhs(const fde_plan* plan, const double* u_prev, const double* f,
+                        double* b, void* stream);
+
+/* Scalars the plan derived from the problem: c0, sr, h1^alpha. */
+fde_status fde_plan_scalars(const fde_plan* plan, double* c0, double* sr, double* h_alpha);
+
+void fde_plan_destroy(fde_plan* plan);
+const char* fde_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDE_H */

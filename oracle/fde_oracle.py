@@ -282,6 +282,18 @@ class Problem2D:
         Ay = self.ep.reshape(-1)[:, None] * np.kron(Tb, I1) + self.em.reshape(-1)[:, None] * np.kron(Tb.T, I1)
         return self.c0 * np.eye(self.N) + Ax + self.sr * Ay
 
+    def matvec_entries(self, x: np.ndarray, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
+        """Selected entries (y_j, x_i) of M x, each summed from its row of the
+        x-line and y-line Toeplitz products."""
+        U = np.asarray(x, dtype=np.float64).reshape(self.n2, self.n1)
+        Ta, Tb = self.Ta(), self.Tb()
+        out = np.empty(len(rows))
+        for t, (j, i) in enumerate(zip(rows, cols)):
+            ax = self.dp[j, i] * (Ta[i] @ U[j]) + self.dm[j, i] * (Ta[:, i] @ U[j])
+            ay = self.ep[j, i] * (Tb[j] @ U[:, i]) + self.em[j, i] * (Tb[:, j] @ U[:, i])
+            out[t] = self.c0 * U[j, i] + ax + self.sr * ay
+        return out
+
     def matvec(self, x: np.ndarray) -> np.ndarray:
         """The Kronecker products applied as matrix products on the (n2, n1)
         grid: (I (x) A) u <-> U A^T, (B (x) I) u <-> B U."""
@@ -376,7 +388,7 @@ class Tau2D:
     def tau_inv(self, r: np.ndarray) -> np.ndarray:
         n2, n1 = self.F.shape
         R = np.asarray(r, dtype=np.float64).reshape(n2, n1)
-        if max(n1, n2) <= 4096:
+        if max(n1, n2) <= 1024:
             S1, S2 = sine_matrix(n1), sine_matrix(n2)
             Z = S2 @ ((S2 @ R @ S1) / self.F) @ S1
         else:

@@ -1,0 +1,652 @@
+// Host side of libfde: validation, workspace layout, symbol assembly kernels
+// and the C ABI declared in include/fde.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "launch.h"
+
+using namespace fde;
+
+struct fde_plan {
+    fde_problem prob;
+    fde_solve_opts opts;
+    Inst inst;              // host copy of the device record
+    Inst* inst_dev;
+    SyncArea* sync_dev;
+    void* ws;
+    size_t ws_bytes;
+    int device;
+    int smem_bytes;
+    int grid[3];            // co-resident CTAs of each engine mode
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// ---------------------------------------------------------------------------
+// Per-device engine preparation (kernel attributes and occupancy)
+// ---------------------------------------------------------------------------
+
+struct DeviceInfo {
+    bool ready = false;
+    int num_sms = 0;
+    int smem_bytes = 0;
+    int grid[3] = {0, 0, 0};
+};
+std::mutex g_mu;
+DeviceInfo g_dev[64];
+
+cudaError_t prepare_device(int dev, DeviceInfo** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    DeviceInfo& d = g_dev[dev];
+    if (!d.ready) {
+        int sms = 0, optin = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        // leave room for the kernel's static shared memory (instance record, reductions)
+        int smem = optin - 4096;
+        if (smem > 224 * 1024) smem = 224 * 1024;
+        smem &= ~255;
+        for (int mode = 0; mode < 3; ++mode) {
+            KernelInfo ki{};
+            e = mode == 0 ? engine_prepare_f64(smem, &ki)
+                          : (mode == 1 ? engine_prepare_f32(smem, &ki) : engine_prepare_ir(smem, &ki));
+            if (e != cudaSuccess) return e;
+            if (ki.blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+            int g = ki.blocks_per_sm * sms;
+            if (g > kMaxCtas) g = kMaxCtas;
+            d.grid[mode] = g;
+        }
+        d.num_sms = sms;
+        d.smem_bytes = smem;
+        d.ready = true;
+    }
+    *out = &d;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Validation and derived quantities
+// ---------------------------------------------------------------------------
+
+bool valid_order(double a) { return std::isfinite(a) && a > 1.0 && a < 2.0; }
+
+bool coeff_ok(const double* arr, double c) { return arr != nullptr || (std::isfinite(c) && c >= 0.0); }
+
+fde_status validate(const fde_problem* p, const fde_solve_opts* o) {
+    if (!p || !o) return FDE_EINVAL;
+    if (p->dim != 1 && p->dim != 2) return FDE_EINVAL;
+    if (p->n1 < 1 || !is_pow2((long long)p->n1 + 1) || p->n1 + 1 > (1 << 22)) return FDE_EINVAL;
+    if (!valid_order(p->alpha)) return FDE_EINVAL;
+    if (!(p->len1 > 0.0) || !std::isfinite(p->len1) || !(p->dt > 0.0) || !std::isfinite(p->dt)) return FDE_EINVAL;
+    if (p->scheme != FDE_SCHEME_IMPLICIT_EULER && p->scheme != FDE_SCHEME_CRANK_NICOLSON) return FDE_EINVAL;
+    if (p->weights != FDE_WEIGHTS_GL1 && p->weights != FDE_WEIGHTS_WSGD2) return FDE_EINVAL;
+    if (p->order != FDE_ORDER_TAU_D && p->order != FDE_ORDER_D_TAU) return FDE_EINVAL;
+    if (p->tau_shift != 0 && p->tau_shift != 1) return FDE_EINVAL;
+    if (!coeff_ok(p->dp, p->dp_const) || !coeff_ok(p->dm, p->dm_const)) return FDE_EINVAL;
+    if (p->dim == 2) {
+        if (p->n2 < 1 || !is_pow2((long long)p->n2 + 1) || p->n2 + 1 > 4096) return FDE_EINVAL;
+        if (p->n1 + 1 > 4096) return FDE_EINVAL;
+        if (!valid_order(p->beta)) return FDE_EINVAL;
+        if (!(p->len2 > 0.0) || !std::isfinite(p->len2)) return FDE_EINVAL;
+        if (!coeff_ok(p->ep, p->ep_const) || !coeff_ok(p->em, p->em_const)) return FDE_EINVAL;
+    }
+    if (p->tau_shift) {
+        if (p->dp || p->dm) return FDE_EINVAL;                          // constants only
+        if (!(p->dp_const + p->dm_const > 0.0)) return FDE_EINVAL;
+        if (p->dim == 2 && (p->ep || p->em || !(p->ep_const + p->em_const > 0.0))) return FDE_EINVAL;
+    } else {
+        // D = mean of the coefficients must be invertible; arrays are checked by the caller
+        if (!p->dp && !p->dm && !(p->dp_const + p->dm_const > 0.0) && p->dim == 1) return FDE_EINVAL;
+    }
+    if (o->method != FDE_PCG && o->method != FDE_GMRES) return FDE_EINVAL;
+    if (o->method == FDE_GMRES && (o->restart < 1 || o->restart > kMaxRestart)) return FDE_EINVAL;
+    if (!(o->tol > 0.0) || !std::isfinite(o->tol) || o->max_iters < 1) return FDE_EINVAL;
+    if (o->precision < FDE_PREC_F64 || o->precision > FDE_PREC_F32_IR) return FDE_EINVAL;
+    if (o->precision == FDE_PREC_F32_IR && (!(o->inner_tol > 0.0) || o->inner_tol >= 1.0 || o->max_outer < 1))
+        return FDE_EINVAL;
+    if (o->side != FDE_SIDE_RIGHT && o->side != FDE_SIDE_LEFT) return FDE_EINVAL;
+    if (o->method == FDE_PCG) {
+        // PCG needs a symmetric M (d_+ = d_-, e_+ = e_-) and a symmetric positive P (D constant)
+        const bool symx = p->dp == p->dm && (p->dp != nullptr || p->dp_const == p->dm_const);
+        const bool symy = p->dim == 1 || (p->ep == p->em && (p->ep != nullptr || p->ep_const == p->em_const));
+        const bool constD = !p->dp && !p->dm && (p->dim == 1 || (!p->ep && !p->em));
+        if (!symx || !symy || !(p->tau_shift || constD)) return FDE_EINVAL;
+    }
+    return FDE_OK;
+}
+
+struct Layout {
+    size_t inst, sync, tw64, tw32;
+    size_t lam64[2], lam32[2], phi64[2], phi32[2];
+    size_t dinv64, dinv32, dp32, dm32, ep32, em32;
+    size_t r64, t64, wvec, split64, split32, wts;
+    size_t total;
+    int TW, logTW;
+    int Np[2];
+    bool has_D;
+};
+
+bool compute_has_D(const fde_problem* p) { return !p->tau_shift; }
+
+Layout layout(const fde_problem* p, const fde_solve_opts* o) {
+    Layout L{};
+    const long long N = (long long)p->n1 * (p->dim == 2 ? p->n2 : 1);
+    L.Np[0] = p->n1 + 1;
+    L.Np[1] = p->dim == 2 ? p->n2 + 1 : 1;
+    const int Lmax = 2 * std::max(L.Np[0], L.Np[1]);
+    L.TW = std::max(Lmax, 16);
+    L.logTW = ilog2(L.TW);
+    L.has_D = compute_has_D(p);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes); return at; };
+    L.inst = take(sizeof(Inst));
+    L.sync = take(sizeof(SyncArea));
+    L.tw64 = take((size_t)L.TW * sizeof(cx<double>));
+    L.tw32 = take((size_t)L.TW * sizeof(cx<float>));
+    for (int a = 0; a < p->dim; ++a) {
+        const size_t np1 = (size_t)L.Np[a] + 1;
+        L.lam64[a] = take(np1 * sizeof(cx<double>));
+        L.lam32[a] = take(np1 * sizeof(cx<float>));
+        L.phi64[a] = take(np1 * sizeof(double));
+        L.phi32[a] = take(np1 * sizeof(float));
+    }
+    L.dinv64 = L.has_D ? take(N * sizeof(double)) : 0;
+    L.dinv32 = L.has_D ? take(N * sizeof(float)) : 0;
+    L.dp32 = p->dp ? take(N * sizeof(float)) : 0;
+    L.dm32 = p->dm ? (p->dm == p->dp ? L.dp32 : take(N * sizeof(float))) : 0;
+    L.ep32 = (p->dim == 2 && p->ep) ? take(N * sizeof(float)) : 0;
+    L.em32 = (p->dim == 2 && p->em) ? (p->em == p->ep ? L.ep32 : take(N * sizeof(float))) : 0;
+    L.r64 = take(N * sizeof(double));
+    L.t64 = take(N * sizeof(double));
+    const size_t wsz = o->precision == FDE_PREC_F64 ? sizeof(double) : sizeof(float);
+    const long long nvec = o->method == FDE_GMRES ? (o->restart + 4) : 5;
+    const long long extra = o->precision == FDE_PREC_F64 ? 0 : 2;
+    L.wvec = take((size_t)(nvec + extra) * N * wsz);
+    const int npmax = std::max(L.Np[0], L.Np[1]);
+    L.split64 = take((size_t)2 * npmax * sizeof(cx<double>));
+    L.split32 = take((size_t)2 * npmax * sizeof(cx<float>));
+    L.wts = take((size_t)(npmax + 2) * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// Assembly kernels (FP64)
+// ---------------------------------------------------------------------------
+
+__global__ void k_twiddles(cx<double>* tw64, cx<float>* tw32, int TW) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < TW; t += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)t / (double)TW, &s, &c);
+        tw64[t] = mk(c, s);
+        tw32[t] = mk((float)c, (float)s);
+    }
+}
+
+struct AxisJob {
+    int n, Np, logNp, logTW, weights;
+    double alpha;
+    int kind;              // 0: 1D tau multiplier 1/(L (add + mult F)); 1: 2D axis part add + mult F
+    double add, mult;
+    const cx<double>* tw64;
+    cx<double>* lam64;
+    cx<float>* lam32;
+    double* phi64;
+    float* phi32;
+    double* wts;
+    cx<double>* bufA;
+    cx<double>* bufB;
+};
+
+// F_alpha(theta_j), theta_j = j pi / Np: p_alpha (first order) or q_alpha
+// (WSGD).  With 1 - e^{i t} = 2 sin(t/2) e^{i (t - pi)/2}:
+//   p = -2 rho cos(psi - t),  q = -rho [(2 - a + a cos t) cos psi + a sin t sin psi],
+//   rho = (2 sin(t/2))^a, psi = a (t - pi)/2.
+__device__ double symbol_sample(double a, int weights, int j, int Np) {
+    const double u = (double)j / (double)Np;        // t / pi
+    const double rho = pow(2.0 * sinpi(0.5 * u), a);
+    const double psi = 0.5 * a * (u - 1.0);         // psi / pi
+    if (weights == FDE_WEIGHTS_GL1) return -2.0 * rho * cospi(psi - u);
+    return -rho * ((2.0 - a + a * cospi(u)) * cospi(psi) + a * sinpi(u) * sinpi(psi));
+}
+
+__global__ void __launch_bounds__(1024) k_axis(AxisJob J) {
+    const int n = J.n, Np = J.Np;
+    const int L = 2 * Np;
+    if (threadIdx.x == 0) {
+        // weights w_0..w_{n+1}: g_k = (-1)^k binom(alpha, k) by the running product,
+        // WSGD w_k = (alpha/2) g_k + ((2-alpha)/2) g_{k-1}
+        double gprev = 1.0;
+        J.wts[0] = J.weights == FDE_WEIGHTS_GL1 ? 1.0 : 0.5 * J.alpha;
+        for (int k = 1; k <= n + 1; ++k) {
+            const double g = gprev * (-(J.alpha - k + 1.0) / k);
+            J.wts[k] = J.weights == FDE_WEIGHTS_GL1 ? g : 0.5 * J.alpha * g + 0.5 * (2.0 - J.alpha) * gprev;
+            gprev = g;
+        }
+    }
+    __syncthreads();
+    // first column of the L-circulant embedding T: c_k = -w_{k+1} (k < n), c_{L-1} = -w_0
+    for (int m = threadIdx.x; m < Np; m += blockDim.x) {
+        double c[2];
+        for (int e = 0; e < 2; ++e) {
+            const int k = 2 * m + e;
+            c[e] = k < n ? -J.wts[k + 1] : (k == L - 1 ? -J.wts[0] : 0.0);
+        }
+        J.bufA[m] = mk(c[0], c[1]);
+    }
+    __syncthreads();
+    cx<double>* Z = fft_pingpong<double, false>(J.bufA, J.bufB, J.logNp, J.tw64, J.logTW);
+    const int wsh = J.logTW - (J.logNp + 1);
+    const double invL = 1.0 / (double)L;
+    for (int j = threadIdx.x; j <= Np / 2; j += blockDim.x) {
+        const int jm = (Np - j) & (Np - 1);
+        cx<double> a, b;
+        unpack_pair(Z[j], Z[jm], J.tw64[j << wsh], a, b);
+        J.lam64[j] = invL * a;
+        J.lam64[Np - j] = invL * conj(b);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j <= Np; j += blockDim.x) {
+        const cx<double> l = J.lam64[j];
+        J.lam32[j] = mk((float)l.x, (float)l.y);
+        double v = 0.0;
+        if (j >= 1 && j <= n) {
+            const double F = symbol_sample(J.alpha, J.weights, j, Np);
+            v = J.kind == 0 ? invL / (J.add + J.mult * F) : J.add + J.mult * F;
+        }
+        J.phi64[j] = v;
+        J.phi32[j] = (float)v;
+    }
+}
+
+struct VecJob {
+    long long N;
+    int dim, has_D;
+    const double *dp, *dm, *ep, *em;
+    double dpc, dmc, epc, emc;
+    double* dinv64;
+    float* dinv32;
+    float *dp32, *dm32, *ep32, *em32;
+};
+
+__global__ void k_vectors(VecJob J) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < J.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double dp = J.dp ? J.dp[i] : J.dpc;
+        const double dm = J.dm ? J.dm[i] : J.dmc;
+        if (J.dp32) J.dp32[i] = (float)dp;
+        if (J.dm32 && J.dm32 != J.dp32) J.dm32[i] = (float)dm;
+        double D;
+        if (J.dim == 2) {
+            const double ep = J.ep ? J.ep[i] : J.epc;
+            const double em = J.em ? J.em[i] : J.emc;
+            if (J.ep32) J.ep32[i] = (float)ep;
+            if (J.em32 && J.em32 != J.ep32) J.em32[i] = (float)em;
+            D = 0.25 * (dp + dm + ep + em);
+        } else {
+            D = 0.5 * (dp + dm);
+        }
+        if (J.has_D) {
+            const double di = 1.0 / D;
+            J.dinv64[i] = di;
+            J.dinv32[i] = (float)di;
+        }
+    }
+}
+
+__global__ void k_write_inst(Inst v, Inst* dst) { *dst = v; }
+
+__global__ void k_step_rhs(long long N, double c0, double ha, const double* u, const double* f, double* b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        b[i] = c0 * u[i] + (f ? ha * f[i] : 0.0);
+}
+
+template <typename T>
+T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + off); }
+
+int line_modes(const fde_problem* p, const Layout& Lo, int work_bytes) {
+    if (p->dim == 2) return kPlane | (kPlane << 8);
+    const int Np = Lo.Np[0];
+    const bool sym = p->dp == p->dm && (p->dp != nullptr || p->dp_const == p->dm_const);
+    const int nbuf = sym ? 1 : 2;
+    auto fits = [&](int ept, int esz) {
+        return Np * nbuf <= ept * kThreads && (long long)Np * nbuf * esz <= work_bytes &&
+               (long long)Np * esz <= work_bytes;
+    };
+    const int m64 = fits(Ept<double>::v, (int)sizeof(cx<double>)) ? kLineCta : kLineSplit;
+    const int m32 = fits(Ept<float>::v, (int)sizeof(cx<float>)) ? kLineCta : kLineSplit;
+    return m64 | (m32 << 8);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void fde_default_opts(fde_solve_opts* o) {
+    if (!o) return;
+    o->method = FDE_GMRES;
+    o->restart = 30;
+    o->tol = 1e-8;
+    o->max_iters = 5000;
+    o->precision = FDE_PREC_F64;
+    o->inner_tol = 1e-4;
+    o->max_outer = 50;
+    o->side = FDE_SIDE_RIGHT;
+}
+
+const char* fde_status_string(int s) {
+    switch (s) {
+        case FDE_OK: return "ok";
+        case FDE_EINVAL: return "invalid argument";
+        case FDE_ENOMEM: return "workspace too small";
+        case FDE_ECUDA: return "CUDA error";
+        case FDE_ENOCONV: return "no convergence within the iteration cap";
+        case FDE_EBREAKDOWN: return "Krylov breakdown";
+        case FDE_ETIMEOUT: return "inter-CTA barrier timed out";
+        case FDE_ENONFINITE: return "non-finite value in a reduction";
+        default: return "unknown status";
+    }
+}
+
+fde_status fde_workspace_size(const fde_problem* prob, const fde_solve_opts* opts, size_t* bytes) {
+    if (!bytes) return FDE_EINVAL;
+    const fde_status s = validate(prob, opts);
+    if (s != FDE_OK) return s;
+    *bytes = layout(prob, opts).total;
+    return FDE_OK;
+}
+
+fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* opts, void* workspace, size_t bytes,
+                               fde_plan** plan_out, void* stream) {
+    if (!plan_out || !workspace) return FDE_EINVAL;
+    *plan_out = nullptr;
+    fde_status s = validate(prob, opts);
+    if (s != FDE_OK) return s;
+    if ((reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)) != 0) return FDE_EINVAL;
+    const Layout Lo = layout(prob, opts);
+    if (bytes < Lo.total) return FDE_ENOMEM;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FDE_ECUDA;
+    DeviceInfo* di = nullptr;
+    if (prepare_device(dev, &di) != cudaSuccess) return FDE_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    fde_plan* p = new (std::nothrow) fde_plan();
+    if (!p) return FDE_ENOMEM;
+    p->prob = *prob;
+    p->opts = *opts;
+    p->ws = workspace;
+    p->ws_bytes = bytes;
+    p->device = dev;
+    p->smem_bytes = di->smem_bytes;
+    for (int i = 0; i < 3; ++i) p->grid[i] = di->grid[i];
+
+    const int m = opts->method == FDE_GMRES ? opts->restart : 1;
+    const int work_bytes = di->smem_bytes - (int)kshared_bytes(m);
+
+    Inst& I = p->inst;
+    std::memset(&I, 0, sizeof(Inst));
+    I.dim = prob->dim;
+    I.n1 = prob->n1;
+    I.n2 = prob->dim == 2 ? prob->n2 : 1;
+    I.N = (long long)I.n1 * I.n2;
+    I.line_mode = line_modes(prob, Lo, work_bytes);
+    I.symx = prob->dp == prob->dm && (prob->dp != nullptr || prob->dp_const == prob->dm_const);
+    I.symy = prob->dim == 2 && prob->ep == prob->em && (prob->ep != nullptr || prob->ep_const == prob->em_const);
+    I.has_D = Lo.has_D;
+    I.order = prob->order;
+    I.shift = prob->tau_shift;
+    I.weights = prob->weights;
+    I.method = opts->method;
+    I.precision = opts->precision;
+    I.restart = opts->method == FDE_GMRES ? opts->restart : 0;
+    const double h1 = prob->len1 / (prob->n1 + 1);
+    const double ha = std::pow(h1, prob->alpha);
+    I.h_alpha = ha;
+    I.c0 = (prob->scheme == FDE_SCHEME_CRANK_NICOLSON ? 2.0 : 1.0) * ha / prob->dt;
+    if (prob->dim == 2) {
+        const double h2 = prob->len2 / (prob->n2 + 1);
+        I.sr = ha / std::pow(h2, prob->beta);
+        I.phi_scale2d = 1.0 / ((double)(prob->n1 + 1) * (double)(prob->n2 + 1));
+    }
+    I.logTW = Lo.logTW;
+    I.tw64 = at<cx<double>>(workspace, Lo.tw64);
+    I.tw32 = at<cx<float>>(workspace, Lo.tw32);
+    for (int a = 0; a < prob->dim; ++a) {
+        AxisData& A = I.ax[a];
+        A.n = a == 0 ? prob->n1 : prob->n2;
+        A.Np = A.n + 1;
+        A.logNp = ilog2(A.Np);
+        A.logP1 = A.logNp / 2;
+        A.logP2 = A.logNp - A.logP1;
+        A.P1 = 1 << A.logP1;
+        A.P2 = 1 << A.logP2;
+        A.lam64 = at<cx<double>>(workspace, Lo.lam64[a]);
+        A.lam32 = at<cx<float>>(workspace, Lo.lam32[a]);
+        A.phi64 = at<double>(workspace, Lo.phi64[a]);
+        A.phi32 = at<float>(workspace, Lo.phi32[a]);
+    }
+    I.dp64 = prob->dp;
+    I.dm64 = prob->dm;
+    I.ep64 = prob->dim == 2 ? prob->ep : nullptr;
+    I.em64 = prob->dim == 2 ? prob->em : nullptr;
+    I.dpc = prob->dp_const;
+    I.dmc = prob->dm_const;
+    I.epc = prob->ep_const;
+    I.emc = prob->em_const;
+    I.dp32 = Lo.dp32 ? at<float>(workspace, Lo.dp32) : nullptr;
+    I.dm32 = Lo.dm32 ? at<float>(workspace, Lo.dm32) : nullptr;
+    I.ep32 = Lo.ep32 ? at<float>(workspace, Lo.ep32) : nullptr;
+    I.em32 = Lo.em32 ? at<float>(workspace, Lo.em32) : nullptr;
+    I.dinv64 = Lo.has_D ? at<double>(workspace, Lo.dinv64) : nullptr;
+    I.dinv32 = Lo.has_D ? at<float>(workspace, Lo.dinv32) : nullptr;
+    I.wvec = at<void>(workspace, Lo.wvec);
+    I.r64 = at<double>(workspace, Lo.r64);
+    I.t64 = at<double>(workspace, Lo.t64);
+    I.split64 = at<void>(workspace, Lo.split64);
+    I.split32 = at<void>(workspace, Lo.split32);
+    p->inst_dev = at<Inst>(workspace, Lo.inst);
+    p->sync_dev = at<SyncArea>(workspace, Lo.sync);
+
+    // --- device assembly, all on `st` ---
+    k_twiddles<<<std::min(1024, (Lo.TW + 255) / 256), 256, 0, st>>>(const_cast<cx<double>*>(I.tw64),
+                                                                     const_cast<cx<float>*>(I.tw32), Lo.TW);
+    const bool shift = prob->tau_shift != 0;
+    const double dbar = 0.5 * (prob->dp_const + prob->dm_const);
+    const double ebar = 0.5 * (prob->ep_const + prob->em_const);
+    for (int a = 0; a < prob->dim; ++a) {
+        AxisJob J{};
+        const AxisData& A = I.ax[a];
+        J.n = A.n;
+        J.Np = A.Np;
+        J.logNp = A.logNp;
+        J.logTW = Lo.logTW;
+        J.weights = prob->weights;
+        J.alpha = a == 0 ? prob->alpha : prob->beta;
+        if (prob->dim == 1) {
+            // P_F (Sec. 3.1): 1/(L F); Case I (Sec. 3.1.1): D tau(F + 2 nu/(d_+ + d_-)) = tau(nu + dbar F)
+            J.kind = 0;
+            J.add = shift ? I.c0 : 0.0;
+            J.mult = shift ? dbar : 1.0;
+        } else {
+            // Sec. 3.2: F = F_a + sr F_b, or P_hat's c0 + d F_a + sr e F_b, split per axis
+            J.kind = 1;
+            if (a == 0) { J.add = shift ? I.c0 : 0.0; J.mult = shift ? dbar : 1.0; }
+            else { J.add = 0.0; J.mult = shift ? I.sr * ebar : I.sr; }
+        }
+        J.tw64 = I.tw64;
+        J.lam64 = const_cast<cx<double>*>(A.lam64);
+        J.lam32 = const_cast<cx<float>*>(A.lam32);
+        J.phi64 = const_cast<double*>(A.phi64);
+        J.phi32 = const_cast<float*>(A.phi32);
+        J.wts = at<double>(workspace, Lo.wts);
+        J.bufA = at<cx<double>>(workspace, Lo.split64);
+        J.bufB = J.bufA + std::max(Lo.Np[0], Lo.Np[1]);
+        k_axis<<<1, 1024, 0, st>>>(J);
+    }
+    VecJob V{};
+    V.N = I.N;
+    V.dim = prob->dim;
+    V.has_D = Lo.has_D;
+    V.dp = prob->dp;
+    V.dm = prob->dm;
+    V.ep = I.ep64;
+    V.em = I.em64;
+    V.dpc = prob->dp_const;
+    V.dmc = prob->dm_const;
+    V.epc = prob->ep_const;
+    V.emc = prob->em_const;
+    V.dinv64 = const_cast<double*>(I.dinv64);
+    V.dinv32 = const_cast<float*>(I.dinv32);
+    V.dp32 = const_cast<float*>(I.dp32);
+    V.dm32 = const_cast<float*>(I.dm32);
+    V.ep32 = const_cast<float*>(I.ep32);
+    V.em32 = const_cast<float*>(I.em32);
+    const int vblocks = (int)std::min<long long>(4096, (I.N + 255) / 256);
+    k_vectors<<<vblocks, 256, 0, st>>>(V);
+    k_write_inst<<<1, 1, 0, st>>>(I, p->inst_dev);
+    if (cudaGetLastError() != cudaSuccess) {
+        delete p;
+        return FDE_ECUDA;
+    }
+    *plan_out = p;
+    return FDE_OK;
+}
+
+void fde_plan_destroy(fde_plan* p) { delete p; }
+
+fde_status fde_plan_scalars(const fde_plan* p, double* c0, double* sr, double* h_alpha) {
+    if (!p) return FDE_EINVAL;
+    if (c0) *c0 = p->inst.c0;
+    if (sr) *sr = p->inst.sr;
+    if (h_alpha) *h_alpha = p->inst.h_alpha;
+    return FDE_OK;
+}
+
+static fde_status launch_op(const fde_plan* p, int op, int dtype, const void* in, void* out, void* stream) {
+    if (!p || !in || !out || in == out) return FDE_EINVAL;
+    if (dtype != FDE_F64 && dtype != FDE_F32) return FDE_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    EngineArgs* a = new (std::nothrow) EngineArgs();
+    if (!a) return FDE_ENOMEM;
+    a->op = op;
+    a->count = 1;
+    a->dtype = dtype;
+    a->smem_bytes = p->smem_bytes;
+    a->sync = p->sync_dev;
+    a->info = nullptr;
+    a->inst[0] = p->inst_dev;
+    a->in[0] = in;
+    a->out[0] = out;
+    a->order[0] = 0;
+    const int mode = dtype == FDE_F64 ? kModeF64 : kModeF32;
+    const int lm = dtype == FDE_F64 ? (p->inst.line_mode & 0xff) : ((p->inst.line_mode >> 8) & 0xff);
+    int grid = p->grid[mode];
+    if (p->inst.dim == 1 && lm == kLineCta) grid = 1;
+    a->team_size = grid;
+    cudaError_t e = cudaMemsetAsync(p->sync_dev, 0, offsetof(SyncArea, partial), st);
+    if (e == cudaSuccess) e = mode == kModeF64 ? engine_launch_f64(*a, grid, st) : engine_launch_f32(*a, grid, st);
+    delete a;
+    return e == cudaSuccess ? FDE_OK : FDE_ECUDA;
+}
+
+fde_status fde_toeplitz_matvec(const fde_plan* p, int dtype, const void* x, void* y, void* stream) {
+    return launch_op(p, kOpMatvec, dtype, x, y, stream);
+}
+
+fde_status fde_tau_solve(const fde_plan* p, int dtype, const void* r, void* z, void* stream) {
+    return launch_op(p, kOpTau, dtype, r, z, stream);
+}
+
+fde_status fde_krylov_solve(const fde_plan* const* plans, int count, const double* const* b, double* const* x,
+                            const fde_solve_opts* opts, fde_solve_info* info_dev, void* stream) {
+    if (!plans || !b || !x || !opts || !info_dev || count < 1 || count > kMaxBatch) return FDE_EINVAL;
+    const fde_plan* p0 = plans[0];
+    if (!p0) return FDE_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const fde_plan* p = plans[i];
+        if (!p || !b[i] || !x[i] || (const void*)b[i] == (const void*)x[i]) return FDE_EINVAL;
+        if (p->opts.method != p0->opts.method || p->opts.precision != p0->opts.precision ||
+            p->opts.restart != p0->opts.restart || p->device != p0->device)
+            return FDE_EINVAL;
+    }
+    if (!(opts->tol > 0.0) || opts->max_iters < 1 || (opts->side != FDE_SIDE_RIGHT && opts->side != FDE_SIDE_LEFT))
+        return FDE_EINVAL;
+    if (p0->opts.precision == FDE_PREC_F32_IR && (!(opts->inner_tol > 0.0) || opts->max_outer < 1)) return FDE_EINVAL;
+    const int mode = p0->opts.precision;
+    EngineArgs* a = new (std::nothrow) EngineArgs();
+    if (!a) return FDE_ENOMEM;
+    a->op = kOpSolve;
+    a->count = count;
+    a->dtype = FDE_F64;
+    a->smem_bytes = p0->smem_bytes;
+    a->sync = p0->sync_dev;
+    a->info = info_dev;
+    a->tol = opts->tol;
+    a->inner_tol = opts->inner_tol;
+    a->max_iters = opts->max_iters;
+    a->max_outer = opts->max_outer;
+    a->side = opts->side;
+    bool all_cta = true;
+    std::vector<int> idx(count);
+    for (int i = 0; i < count; ++i) {
+        const fde_plan* p = plans[i];
+        a->inst[i] = p->inst_dev;
+        a->in[i] = b[i];
+        a->out[i] = x[i];
+        idx[i] = i;
+        const int lm = mode == FDE_PREC_F64 ? (p->inst.line_mode & 0xff) : ((p->inst.line_mode >> 8) & 0xff);
+        if (!(p->inst.dim == 1 && lm == kLineCta)) all_cta = false;
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int u, int v) { return plans[u]->inst.N > plans[v]->inst.N; });
+    for (int i = 0; i < count; ++i) a->order[i] = (unsigned short)idx[i];
+    const int G = p0->grid[mode];
+    int grid, ts;
+    if (all_cta) {
+        ts = 1;
+        grid = std::min(G, count);
+    } else if (count >= G) {
+        ts = 1;
+        grid = G;
+    } else {
+        ts = G / count;
+        grid = ts * count;
+    }
+    a->team_size = ts;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(p0->sync_dev, 0, offsetof(SyncArea, partial), st);
+    if (e == cudaSuccess) {
+        if (mode == FDE_PREC_F64) e = engine_launch_f64(*a, grid, st);
+        else if (mode == FDE_PREC_F32) e = engine_launch_f32(*a, grid, st);
+        else e = engine_launch_ir(*a, grid, st);
+    }
+    delete a;
+    return e == cudaSuccess ? FDE_OK : FDE_ECUDA;
+}
+
+fde_status fde_step_rhs(const fde_plan* p, const double* u_prev, const double* f, double* b, void* stream) {
+    if (!p || !u_prev || !b || u_prev == b) return FDE_EINVAL;
+    if (p->prob.scheme != FDE_SCHEME_IMPLICIT_EULER) return FDE_EINVAL;
+    const long long N = p->inst.N;
+    const int blocks = (int)std::min<long long>(4096, (N + 255) / 256);
+    k_step_rhs<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(N, p->inst.c0, p->inst.h_alpha, u_prev, f, b);
+    return cudaGetLastError() == cudaSuccess ? FDE_OK : FDE_ECUDA;
+}
+
+}  // extern "C"

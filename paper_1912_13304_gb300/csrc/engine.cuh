@@ -1,0 +1,201 @@
+// The persistent cooperative kernel.  One launch runs a batch of independent
+// solves (or one operator application): CTAs form teams; a team of one CTA
+// pulls instances from a queue (largest first), a team of many CTAs works on
+// one instance at a time with team barriers between phases.
+#pragma once
+
+#include "krylov.cuh"
+
+namespace fde {
+
+enum Op : int { kOpSolve = 0, kOpMatvec = 1, kOpTau = 2 };
+enum Mode : int { kModeF64 = 0, kModeF32 = 1, kModeIR = 2 };
+
+struct EngineArgs {
+    int op;
+    int count;
+    int team_size;
+    int dtype;                 // operator calls: FDE_F64 / FDE_F32
+    int smem_bytes;            // dynamic shared memory of the launch
+    SyncArea* sync;
+    fde_solve_info* info;
+    double tol, inner_tol;
+    int max_iters, max_outer, side;
+    const Inst* inst[kMaxBatch];
+    const void* in[kMaxBatch];
+    void* out[kMaxBatch];
+    unsigned short order[kMaxBatch];
+};
+
+FDE_D int lm_f64(const Inst& I) { return I.line_mode & 0xff; }
+FDE_D int lm_f32(const Inst& I) { return (I.line_mode >> 8) & 0xff; }
+
+// FP64 residual r64 = b - A x and its norm (refinement and FP32 modes).
+static FDE_NI bool residual64(const Team& t, const Inst& I, const double* b, const double* x, KShared& ks,
+                      unsigned char* work, int bytes, double& rn) {
+    if (!op_matvec<double>(t, I, lm_f64(I), x, 1.0, I.t64, I.r64, work, bytes)) return false;
+    long long lo, hi;
+    team_range(t, I.N, lo, hi);
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) I.r64[i] = __ldcg(b + i) - __ldcg(I.t64 + i);
+    if (!team_sync(t)) return false;
+    const double* a[1] = {I.r64};
+    if (!dots_pairs<double, 1>(t, I.N, a, a, ks)) return false;
+    rn = sqrt(ks.red[0]);
+    return true;
+}
+
+template <int MODE>
+FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx, KShared& ks, unsigned char* work,
+                     int bytes) {
+    const double* b = reinterpret_cast<const double*>(a.in[idx]);
+    double* x = reinterpret_cast<double*>(a.out[idx]);
+    SolveState st{};
+    st.status = FDE_ENOCONV;
+    int outer = 0;
+    const long long N = I.N;
+    long long lo, hi;
+    team_range(t, N, lo, hi);
+    if constexpr (MODE == kModeF64) {
+        SolveParams sp{a.tol, a.max_iters, a.side};
+        if (!krylov_core<double>(t, I, lm_f64(I), b, x, sp, st, ks, work, bytes)) return false;
+    } else {
+        float* rhs32 = reinterpret_cast<float*>(I.wvec) + extra_vec_offset<float>(I);
+        float* sol32 = rhs32 + N;
+        {
+            const double* p[1] = {b};
+            if (!dots_pairs<double, 1>(t, N, p, p, ks)) return false;
+        }
+        const double nb = sqrt(ks.red[0]);
+        if constexpr (MODE == kModeF32) {
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                rhs32[i] = float(__ldcg(b + i));
+                sol32[i] = float(x[i]);
+            }
+            if (!team_sync(t)) return false;
+            SolveParams sp{a.tol, a.max_iters, a.side};
+            if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, st, ks, work, bytes)) return false;
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) x[i] = double(sol32[i]);
+            if (!team_sync(t)) return false;
+            double rn;
+            if (!residual64(t, I, b, x, ks, work, bytes, rn)) return false;
+            st.relres = nb > 0.0 ? rn / nb : 0.0;
+        } else {
+            int status = FDE_ENOCONV;
+            int inner_status = FDE_OK;
+            while (true) {
+                double rn;
+                if (!residual64(t, I, b, x, ks, work, bytes, rn)) return false;
+                st.relres = nb > 0.0 ? rn / nb : 0.0;
+                if (!finite(rn)) { status = FDE_ENONFINITE; break; }
+                if (rn <= a.tol * nb) { status = FDE_OK; break; }
+                if (outer >= a.max_outer || st.iterations >= a.max_iters) { status = FDE_ENOCONV; break; }
+                if (inner_status == FDE_EBREAKDOWN || inner_status == FDE_ENONFINITE) { status = inner_status; break; }
+                const double inv = 1.0 / rn;
+                for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                    rhs32[i] = float(I.r64[i] * inv);
+                    sol32[i] = 0.0f;
+                }
+                if (!team_sync(t)) return false;
+                SolveState in{};
+                in.iterations = st.iterations;
+                SolveParams sp{a.inner_tol, a.max_iters, a.side};
+                if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, in, ks, work, bytes)) return false;
+                st.iterations = in.iterations;
+                st.restarts += in.restarts;
+                st.relres_est = in.relres_est;
+                inner_status = in.status;
+                for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) x[i] = x[i] + rn * double(sol32[i]);
+                if (!team_sync(t)) return false;
+                ++outer;
+            }
+            st.status = status;
+        }
+    }
+    if (t.rank == 0 && threadIdx.x == 0) {
+        fde_solve_info inf;
+        inf.status = st.status;
+        inf.iterations = st.iterations;
+        inf.outer = outer;
+        inf.restarts = st.restarts;
+        inf.relres = st.relres;
+        inf.relres_est = st.relres_est;
+        a.info[idx] = inf;
+    }
+    return true;
+}
+
+template <int MODE>
+FDE_D bool run_op(const Team& t, const Inst& I, const EngineArgs& a, int idx, unsigned char* work, int bytes) {
+    const bool f64 = (MODE == kModeF64) || a.dtype == FDE_F64;
+    if (f64) {
+        const double* in = reinterpret_cast<const double*>(a.in[idx]);
+        double* out = reinterpret_cast<double*>(a.out[idx]);
+        if (a.op == kOpMatvec) return op_matvec<double>(t, I, lm_f64(I), in, 1.0, out, I.t64, work, bytes);
+        return op_tau<double>(t, I, lm_f64(I), in, 1.0, out, work, bytes);
+    }
+    if constexpr (MODE != kModeF64) {
+        const float* in = reinterpret_cast<const float*>(a.in[idx]);
+        float* out = reinterpret_cast<float*>(a.out[idx]);
+        float* tmp = reinterpret_cast<float*>(I.t64);
+        if (a.op == kOpMatvec) return op_matvec<float>(t, I, lm_f32(I), in, 1.0f, out, tmp, work, bytes);
+        return op_tau<float>(t, I, lm_f32(I), in, 1.0f, out, work, bytes);
+    }
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant__ EngineArgs a) {
+    extern __shared__ __align__(256) unsigned char dsm[];
+    __shared__ Inst s_inst;
+    __shared__ unsigned int s_next;
+    const int ts = a.team_size;
+    const int nteams = gridDim.x / ts;
+    const int team_id = blockIdx.x / ts;
+    if (team_id >= nteams) return;
+    Team t;
+    t.rank = blockIdx.x - team_id * ts;
+    t.size = ts;
+    t.count = &a.sync->bar_count[team_id];
+    t.gen = &a.sync->bar_gen[team_id];
+    t.partial = a.sync->partial + (size_t)team_id * ts * kMaxDots;
+    t.abort_flag = &a.sync->abort_flag;
+    int next_static = team_id;
+    while (true) {
+        int idx;
+        if (ts == 1) {
+            if (threadIdx.x == 0) s_next = atomicAdd(&a.sync->queue, 1u);
+            __syncthreads();
+            idx = (int)s_next;
+            __syncthreads();
+        } else {
+            idx = next_static;
+            next_static += nteams;
+        }
+        if (idx >= a.count) break;
+        if (*reinterpret_cast<volatile unsigned int*>(&a.sync->abort_flag)) break;
+        const int inst_i = a.order[idx];
+        {
+            const int* src = reinterpret_cast<const int*>(a.inst[inst_i]);
+            int* dst = reinterpret_cast<int*>(&s_inst);
+            for (int w = threadIdx.x; w < (int)(sizeof(Inst) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+        }
+        __syncthreads();
+        const int m = s_inst.method == FDE_GMRES ? s_inst.restart : 1;
+        const size_t hdr = kshared_bytes(m);
+        KShared ks = kshared_carve(dsm, m);
+        unsigned char* work = dsm + hdr;
+        const int bytes = a.smem_bytes - (int)hdr;
+        bool ok;
+        if (a.op == kOpSolve) ok = run_solve<MODE>(t, s_inst, a, inst_i, ks, work, bytes);
+        else ok = run_op<MODE>(t, s_inst, a, inst_i, work, bytes);
+        if (!ok) {
+            if (threadIdx.x == 0 && t.rank == 0 && a.op == kOpSolve) {
+                a.info[inst_i].status = FDE_ETIMEOUT;
+            }
+            break;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace fde

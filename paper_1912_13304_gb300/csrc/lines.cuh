@@ -1,0 +1,221 @@
+// Line transforms of the two operators, built on the real-packed FFT.
+//
+// A real line r_1..r_n (n = Np - 1) is extended to length L = 2 Np either by
+// zeros (Toeplitz product by circulant embedding) or oddly (DST-I, Sec. 1:
+// v_0 = v_Np = 0, v_{L-k} = -r_k).  The extension is packed into Np complex
+// values z_m = v_{2m} + i v_{2m+1} and transformed with an Np-point FFT; the
+// L-point spectrum follows from the pairs (Z_j, Z_{Np-j}):
+//   E_j = (Z_j + conj Z_{Np-j})/2,  O_j = (Z_j - conj Z_{Np-j})/(2i),
+//   X_j = E_j + w_L^j O_j,  X_{j+Np} = E_j - w_L^j O_j.
+// A Hermitian multiplier mu (mu_{L-k} = conj mu_k) keeps the inverse real:
+//   A_j = mu_j X_j, A_{j+Np} = conj(mu_{Np-j}) X_{j+Np},
+//   Q_j = (A_j + A_{j+Np}) + i w_L^{-j} (A_j - A_{j+Np}),
+// and the Np-point inverse FFT of Q gives a_{2m} + i a_{2m+1}.
+//
+// Operators (multipliers are stored pre-divided by L):
+//   T x      : mu = lambda  (eigenvalues of the circulant embedding T)
+//   T^T x    : mu = conj(lambda)
+//   (T+T^T)x : mu = 2 Re(lambda)
+//   tau^{-1} : mu = 1/(L F(theta_k)) on the odd extension, which equals
+//              S diag(1/F) S (the two sine transforms of Sec. 1)
+//   S r      : the odd-extension spectrum itself, S r = sqrt(2/Np) (-Im X_j / 2)
+#pragma once
+
+#include "fft.cuh"
+#include "team.cuh"
+
+namespace fde {
+
+enum Ext : int { kExtZero = 0, kExtOdd = 1 };
+
+// Loads of data that other CTAs of the team wrote in an earlier phase go
+// through L2 only (ld.global.cg), never a possibly stale L1 line.
+template <typename W>
+FDE_D W ldw(const W* p) { return __ldcg(p); }
+FDE_D cx<double> ldw(const cx<double>* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return mk(v.x, v.y);
+}
+FDE_D cx<float> ldw(const cx<float>* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return mk(v.x, v.y);
+}
+
+// Real input line: r_k = scale * base[(k-1) stride] (* pre[(k-1) stride]).
+template <typename W>
+struct RealIn {
+    const W* base;
+    long long stride;
+    W scale;
+    const W* pre;
+    FDE_D W get(int k) const {
+        const long long o = (long long)(k - 1) * stride;
+        W v = ldw(base + o) * scale;
+        if (pre) v *= __ldg(pre + o);
+        return v;
+    }
+};
+
+template <typename W, int EXT>
+FDE_D W ext_val(const RealIn<W>& in, int k, int n, int Np) {
+    if (k >= 1 && k <= n) return in.get(k);
+    if (EXT == kExtOdd && k > Np) return -in.get(2 * Np - k);
+    return W(0);
+}
+
+template <typename W, int EXT>
+FDE_D cx<W> pack_elem(const RealIn<W>& in, int m, int n, int Np) {
+    return mk(ext_val<W, EXT>(in, 2 * m, n, Np), ext_val<W, EXT>(in, 2 * m + 1, n, Np));
+}
+
+template <typename R>
+FDE_D void unpack_pair(cx<R> Zj, cx<R> Zm, cx<R> wj, cx<R>& a, cx<R>& b) {
+    const cx<R> Zc = conj(Zm);
+    const cx<R> E = R(0.5) * (Zj + Zc);
+    const cx<R> O = mul_mi(R(0.5) * (Zj - Zc));
+    const cx<R> t = wj * O;
+    a = E + t;
+    b = E - t;
+}
+
+template <typename R>
+FDE_D void repack_pair(cx<R> al, cx<R> be, cx<R> wj, cx<R>& Qj, cx<R>& Qm) {
+    const cx<R> s = al + be, d = al - be;
+    Qj = s + mul_i(conj(wj) * d);
+    Qm = conj(s) + mul_i(wj * conj(d));
+}
+
+// Multiplier kinds for the spectral step.
+enum MulKind : int { kMulLam2 = 0, kMulSym = 1, kMulTau1 = 2, kMulTau2 = 3 };
+
+template <typename W>
+struct Mult {
+    int kind;
+    const cx<W>* lam;      // [Np+1]
+    const W* phi;          // kMulTau1: [Np+1] multiplier; kMulTau2: [Np+1] y-axis symbol part
+    const W* a1;           // kMulTau2: x-axis symbol part, indexed by x-frequency
+    W scale2d;             // kMulTau2: 2/(n1+1)/L2
+    int n, Np;
+
+    // Multipliers for the pair (j, Np - j): first output and, for kMulLam2,
+    // the second (conj(lambda)).  `col` is the x-frequency index for kMulTau2.
+    FDE_D void apply(int j, int col, cx<W> a, cx<W> b, cx<W>& al, cx<W>& be, cx<W>& al2,
+                     cx<W>& be2) const {
+        const int jm = Np - j;
+        if (kind == kMulLam2) {
+            const cx<W> lj = lam[j];
+            const cx<W> lm = lam[jm];
+            al = lj * a;
+            be = conj(lm) * b;
+            al2 = conj(lj) * a;
+            be2 = lm * b;
+        } else if (kind == kMulSym) {
+            al = (W(2) * lam[j].x) * a;
+            be = (W(2) * lam[jm].x) * b;
+        } else if (kind == kMulTau1) {
+            al = phi[j] * a;
+            be = phi[jm] * b;
+        } else {
+            const W ax = a1[col + 1];
+            const W pj = (j >= 1 && j <= n) ? scale2d / (ax + phi[j]) : W(0);
+            const W pm = (jm >= 1 && jm <= n) ? scale2d / (ax + phi[jm]) : W(0);
+            al = pj * a;
+            be = pm * b;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Whole lines held by one CTA (shared memory).  B lines of Np complex values
+// at stride Np; `buf2` holds the second output of kMulLam2.
+// ---------------------------------------------------------------------------
+
+// Pack B real lines into buf.  in[l] describes line l.  COLMAJOR maps
+// consecutive threads to consecutive lines (coalesced for strided columns).
+template <typename W, int EXT, bool COLMAJOR, typename InF>
+FDE_D void cta_pack(cx<W>* buf, int B, int n, int Np, InF in_of_line) {
+    const int total = B * Np;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, m;
+        if (COLMAJOR) { l = idx % B; m = idx / B; }
+        else { m = idx % Np; l = idx / Np; }
+        buf[l * Np + m] = pack_elem<W, EXT>(in_of_line(l), m, n, Np);
+    }
+    __syncthreads();
+}
+
+// Spectral step on all pairs of B lines.  col_of_line gives kMulTau2's
+// x-frequency index of a line.
+template <typename W, typename ColF>
+FDE_D void cta_spectral(cx<W>* buf, cx<W>* buf2, int B, int Np, int logNp, const cx<W>* tw, int logTW,
+                        const Mult<W>& mu, ColF col_of_line) {
+    const int half = Np / 2 + 1;
+    const int wsh = logTW - (logNp + 1);
+    const bool two = mu.kind == kMulLam2;
+    for (int idx = threadIdx.x; idx < B * half; idx += blockDim.x) {
+        const int l = idx / half;
+        const int j = idx - l * half;
+        const int jm = (Np - j) & (Np - 1);
+        cx<W>* z = buf + l * Np;
+        const cx<W> wj = tw[j << wsh];
+        cx<W> a, b, al, be, al2, be2;
+        unpack_pair(z[j], z[jm], wj, a, b);
+        mu.apply(j, col_of_line(l), a, b, al, be, al2, be2);
+        cx<W> Qj, Qm;
+        repack_pair(al, be, wj, Qj, Qm);
+        z[j] = Qj;
+        if (jm != j) z[jm] = Qm;
+        if (two) {
+            cx<W>* z2 = buf2 + l * Np;
+            repack_pair(al2, be2, wj, Qj, Qm);
+            z2[j] = Qj;
+            if (jm != j) z2[jm] = Qm;
+        }
+    }
+    __syncthreads();
+}
+
+// Lone DST-I of B lines: after the forward FFT of the odd extension, write
+// the unnormalised sine sums s_j = -Im X_j / 2 (j = 1..n) into the real
+// shared-memory array s (B lines at stride Np).
+template <typename W>
+FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, const cx<W>* tw, int logTW) {
+    const int half = Np / 2 + 1;
+    const int wsh = logTW - (logNp + 1);
+    for (int idx = threadIdx.x; idx < B * half; idx += blockDim.x) {
+        const int l = idx / half;
+        const int j = idx - l * half;
+        const int jm = (Np - j) & (Np - 1);
+        const cx<W>* z = buf + l * Np;
+        cx<W> a, b;
+        unpack_pair(z[j], z[jm], tw[j << wsh], a, b);
+        if (j >= 1) {
+            s[l * Np + j] = W(-0.5) * a.y;
+            if (jm != j) s[l * Np + (Np - j)] = W(0.5) * b.y;
+        }
+    }
+    __syncthreads();
+}
+
+// Unpack q_m = a_{2m} + i a_{2m+1} and hand a_k (k = 1..n) to epi(l, k-1, a_k [, b_k]).
+template <typename W, bool COLMAJOR, bool TWO, typename EpiF>
+FDE_D void cta_unpack(const cx<W>* buf, const cx<W>* buf2, int B, int n, int Np, EpiF epi) {
+    // element k of line l lives in buf[l*Np + k/2] (.x if k even, .y if odd)
+    const int total = B * n;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, p;
+        if (COLMAJOR) { l = idx % B; p = idx / B; }
+        else { p = idx % n; l = idx / n; }
+        const int k = p + 1;
+        const cx<W> q = buf[l * Np + (k >> 1)];
+        const W va = (k & 1) ? q.y : q.x;
+        W vb = W(0);
+        if (TWO) {
+            const cx<W> q2 = buf2[l * Np + (k >> 1)];
+            vb = (k & 1) ? q2.y : q2.x;
+        }
+        epi(l, p, va, vb);
+    }
+}
+
+}  // namespace fde

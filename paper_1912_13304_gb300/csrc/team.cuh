@@ -1,0 +1,116 @@
+// Teams of CTAs that cooperate on one solve inside the persistent cooperative
+// launch: a bounded-wait barrier, deterministic all-reductions of FP64
+// partial sums, and the partition of element ranges among the team's CTAs.
+#pragma once
+
+#include "common.cuh"
+
+namespace fde {
+
+// ~2 s at GB300 clocks.  A barrier that waits longer records FDE_ETIMEOUT in
+// the launch's abort flag and every CTA of the launch winds down.
+constexpr long long kBarrierCycles = 4000000000LL;
+
+struct Team {
+    int rank;              // CTA index inside the team
+    int size;              // CTAs in the team
+    unsigned int* count;
+    unsigned int* gen;
+    double* partial;       // [size][kMaxDots]
+    unsigned int* abort_flag;
+};
+
+FDE_D unsigned int ld_volatile(const unsigned int* p) {
+    return *reinterpret_cast<const volatile unsigned int*>(p);
+}
+
+// Returns false when the launch is being aborted (a barrier timed out).
+FDE_D bool team_sync(const Team& t) {
+    __shared__ int s_ok;
+    if (t.size == 1) {
+        __syncthreads();
+        return true;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int g = ld_volatile(t.gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(t.count, 1u);
+        if (arrived == (unsigned int)t.size - 1u) {
+            atomicExch(t.count, 0u);
+            __threadfence();
+            atomicAdd(t.gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_volatile(t.gen) == g) {
+                if (clock64() - t0 > kBarrierCycles) {
+                    ok = 0;
+                    atomicExch(t.abort_flag, 1u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok && (ld_volatile(t.abort_flag) == 0u);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename R>
+FDE_D R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sums of K per-thread values (K <= 8 at a time), written to
+// out[0..K) in shared memory.  Deterministic: fixed shuffle tree, then a
+// fixed-order sum over warps.
+template <int K>
+FDE_D void block_sum(const double (&v)[K], double* out, double* scratch /* [K*32] smem */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double s = warp_sum(v[k]);
+        if (lane == 0) scratch[k * 32 + warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += scratch[threadIdx.x * 32 + w];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// vals[0..K) (shared memory, this CTA's totals) -> team totals in every CTA.
+FDE_D bool team_allreduce(const Team& t, double* vals, int K) {
+    if (t.size == 1) return true;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) t.partial[t.rank * kMaxDots + k] = vals[k];
+    if (!team_sync(t)) return false;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int k = warp; k < K; k += nw) {
+        double s = 0.0;
+        for (int r = lane; r < t.size; r += 32) s += __ldcg(t.partial + r * kMaxDots + k);
+        s = warp_sum(s);
+        if (lane == 0) vals[k] = s;
+    }
+    __syncthreads();
+    return true;
+}
+
+// [lo, hi) of an N-element vector owned by this CTA for elementwise phases.
+FDE_D void team_range(const Team& t, long long N, long long& lo, long long& hi) {
+    long long chunk = (N + t.size - 1) / t.size;
+    chunk = (chunk + 255) & ~255LL;
+    lo = (long long)t.rank * chunk;
+    hi = lo + chunk;
+    if (hi > N) hi = N;
+    if (lo > N) lo = N;
+}
+
+}  // namespace fde

@@ -18,3 +18,16 @@ def golden():
     import json
     with open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")) as f:
         return json.load(f)
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The built library and torch on cuda:0; skips when no GPU is visible."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1912_13304_gb300 as fde
+    from paper_1912_13304_gb300 import build
+    build.build()
+    fde.lib()
+    return torch

@@ -1,0 +1,181 @@
+"""Parity of the CUDA operators (through the C ABI) with the CPU oracle.
+
+y = M x (fde_toeplitz_matvec) and z = P^{-1} r (fde_tau_solve), element by
+element, for 1D lines held by one CTA and lines split across CTAs, 2D planes,
+both precisions and every preconditioner variant.
+
+Tolerances (max-norm error relative to max |reference|): FP64 1e-11 for the
+matvec and 1e-10 for the tau solve (FFT rounding grows like u log2 L; the tau
+solve divides by symbol samples down to ~h^alpha); FP32 2e-5 and 5e-4.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1912_13304_gb300 as fde
+
+pytestmark = pytest.mark.gpu
+
+TOL = {("mv", "f64"): 1e-11, ("tau", "f64"): 1e-10, ("mv", "f32"): 2e-5, ("tau", "f32"): 5e-4}
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+def coeffs_1d(kind, n):
+    h = 1.0 / (n + 1)
+    x = h * np.arange(1, n + 1)
+    if kind == "var":
+        return 1 + x ** 2, 1 + (1 - x) ** 2
+    if kind == "sym":
+        d = 1 + np.sin(3 * x) ** 2
+        return d, d
+    return np.full(n, 1.3), np.full(n, 1.3)
+
+
+def make_1d(gpu, n, kind, alpha=1.5, dt=1 / 512, weights="gl1", shift=False, order="tau_d", precision="f64"):
+    dp, dm = coeffs_1d(kind, n)
+    h = 1.0 / (n + 1)
+    if kind == "const":
+        plan = fde.Plan(1, n, alpha, dt, dp_const=dp[0], dm_const=dm[0], weights=weights, tau_shift=shift,
+                        order=order, precision=precision)
+    else:
+        plan = fde.Plan(1, n, alpha, dt, dp=dp, dm=dm if kind == "var" else dp, weights=weights, order=order,
+                        precision=precision)
+    prob = oracle.Problem1D(alpha=alpha, n=n, c0=h ** alpha / dt, dp=dp, dm=dm, scheme=weights)
+    return plan, prob
+
+
+def to_dev(gpu, v, dtype):
+    return gpu.tensor(np.asarray(v), dtype=gpu.float64 if dtype == "f64" else gpu.float32, device="cuda")
+
+
+SIZES_1D = [1, 3, 7, 63, 1023, 4095, 8191, 16383]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["var", "sym", "const"])
+@pytest.mark.parametrize("n", SIZES_1D)
+def test_matvec_1d(gpu, n, kind, dtype):
+    plan, prob = make_1d(gpu, n, kind)
+    x = np.random.default_rng(n).uniform(-1, 1, n)
+    y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
+    ref = prob.matvec(x, "direct" if n > 4096 else "dense")
+    assert rel_err(y, ref) < TOL[("mv", dtype)]
+
+
+@pytest.mark.parametrize("weights", ["gl1", "wsgd2"])
+@pytest.mark.parametrize("alpha", [1.1, 1.9])
+def test_matvec_1d_weights_and_orders(gpu, weights, alpha):
+    n = 511
+    plan, prob = make_1d(gpu, n, "var", alpha=alpha, weights=weights)
+    x = np.random.default_rng(3).uniform(-1, 1, n)
+    y = plan.matvec(to_dev(gpu, x, "f64")).cpu().numpy()
+    assert rel_err(y, prob.matvec(x)) < 1e-11
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["tau_d", "d_tau", "shift"])
+@pytest.mark.parametrize("n", SIZES_1D)
+def test_tau_1d(gpu, n, variant, dtype):
+    kind = "const" if variant == "shift" else "var"
+    plan, prob = make_1d(gpu, n, kind, shift=variant == "shift", order="d_tau" if variant == "d_tau" else "tau_d")
+    P = oracle.Tau1D.for_problem(prob, shift=variant == "shift", order="d_tau" if variant == "d_tau" else "tau_d")
+    r = np.random.default_rng(n + 1).uniform(-1, 1, n)
+    z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
+    assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_full_size_1d_line_split_across_ctas(gpu, dtype):
+    """n = 65535 (the variable-coefficient workload): sampled rows of M x by
+    their definition, and the whole tau solve."""
+    n = 65535
+    plan, prob = make_1d(gpu, n, "var", alpha=1.8)
+    rng = np.random.default_rng(11)
+    x = rng.uniform(-1, 1, n)
+    y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
+    rows = np.concatenate([[0, 1, 2, n // 2, n - 2, n - 1], rng.integers(0, n, 40)])
+    ref = prob.matvec_rows(x, rows)
+    scale = np.max(np.abs(prob.matvec_rows(x, rng.integers(0, n, 200))))
+    assert np.max(np.abs(y[rows] - ref)) / scale < TOL[("mv", dtype)]
+    P = oracle.Tau1D.for_problem(prob)
+    z = plan.tau(to_dev(gpu, x, dtype)).double().cpu().numpy()
+    assert rel_err(z, P.apply_inverse(x)) < TOL[("tau", dtype)]
+
+
+SIZES_2D = [(1, 1), (3, 7), (15, 31), (63, 63), (127, 255), (511, 127)]
+
+
+def make_2d(gpu, n1, n2, kind, alpha=1.3, beta=1.8, dt=1 / 256, shift=False, order="tau_d", precision="f64"):
+    h1, h2 = 1.0 / (n1 + 1), 1.0 / (n2 + 1)
+    X, Y = np.meshgrid(h1 * np.arange(1, n1 + 1), h2 * np.arange(1, n2 + 1), indexing="xy")
+    if kind == "var":
+        dp, dm, ep, em = 1 + X + Y, 2 - X, 1 + X * Y, 1 + Y ** 2
+    else:
+        dp = dm = np.full((n2, n1), 1.2)
+        ep = em = np.full((n2, n1), 0.8)
+    if kind == "var":
+        plan = fde.Plan(2, n1, alpha, dt, n2=n2, beta=beta, weights="wsgd2", dp=dp, dm=dm, ep=ep, em=em,
+                        order=order, precision=precision)
+    else:
+        plan = fde.Plan(2, n1, alpha, dt, n2=n2, beta=beta, weights="wsgd2", dp_const=1.2, dm_const=1.2,
+                        ep_const=0.8, em_const=0.8, tau_shift=shift, order=order, precision=precision)
+    prob = oracle.Problem2D(alpha=alpha, beta=beta, n1=n1, n2=n2, c0=h1 ** alpha / dt,
+                            sr=h1 ** alpha / h2 ** beta, dp=dp, dm=dm, ep=ep, em=em, scheme="wsgd2")
+    return plan, prob
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["var", "const"])
+@pytest.mark.parametrize("n1,n2", SIZES_2D)
+def test_matvec_2d(gpu, n1, n2, kind, dtype):
+    plan, prob = make_2d(gpu, n1, n2, kind)
+    x = np.random.default_rng(n1 * n2).uniform(-1, 1, n1 * n2)
+    y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
+    assert rel_err(y, prob.matvec(x)) < TOL[("mv", dtype)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["tau_d", "d_tau", "shift"])
+@pytest.mark.parametrize("n1,n2", SIZES_2D)
+def test_tau_2d(gpu, n1, n2, variant, dtype):
+    kind = "const" if variant == "shift" else "var"
+    order = "d_tau" if variant == "d_tau" else "tau_d"
+    plan, prob = make_2d(gpu, n1, n2, kind, shift=variant == "shift", order=order)
+    P = oracle.Tau2D.for_problem(prob, shift=variant == "shift", order=order)
+    r = np.random.default_rng(n1 + n2).uniform(-1, 1, n1 * n2)
+    z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
+    assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_full_size_2d_plane(gpu, dtype):
+    """4095 x 4095 variable coefficients: sampled entries of M x by their
+    definition; the tau solve in full through the library DST-I."""
+    n = 4095
+    plan, prob = make_2d(gpu, n, n, "var")
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, n * n)
+    y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
+    rows = np.concatenate([[0, 0, n - 1, n - 1, n // 2], rng.integers(0, n, 30)])
+    cols = np.concatenate([[0, n - 1, 0, n - 1, n // 3], rng.integers(0, n, 30)])
+    ref = prob.matvec_entries(x, rows, cols)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(y.reshape(n, n)[rows, cols] - ref)) / scale < TOL[("mv", dtype)]
+    P = oracle.Tau2D.for_problem(prob)
+    z = plan.tau(to_dev(gpu, x, dtype)).double().cpu().numpy()
+    assert rel_err(z, P.apply_inverse(x)) < TOL[("tau", dtype)]
+
+
+def test_step_rhs(gpu):
+    n = 1023
+    plan, prob = make_1d(gpu, n, "var")
+    rng = np.random.default_rng(2)
+    u, f = rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    b = plan.rhs(to_dev(gpu, u, "f64"), to_dev(gpu, f, "f64")).cpu().numpy()
+    h = 1.0 / (n + 1)
+    ref = prob.c0 * u + h ** 1.5 * f
+    assert rel_err(b, ref) < 1e-15

@@ -1,0 +1,194 @@
+"""Parity of the device-resident Krylov solves (fde_krylov_solve) with the
+oracle's textbook PCG / GMRES(m) on the same seeded inputs.
+
+Criteria: iteration counts within +-1 of the oracle's at the same tolerance;
+solutions compared with a tightly converged oracle solution (relres 1e-12):
+relative max-norm error 1e-8 for FP64 and FP32-inner/FP64-outer refinement,
+1e-6 for the pure FP32 inner solve; the true residual reported by the device
+is re-checked with the oracle's matvec.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1912_13304_gb300 as fde
+import workloads
+from test_gpu_ops import make_1d, make_2d, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_problem_1d(w):
+    n = w["n1"]
+    h = w["length"] / (n + 1)
+    return oracle.Problem1D(alpha=w["alpha"], n=n, c0=h ** w["alpha"] / w["dt"], dp=w["dp"], dm=w["dm"],
+                            scheme=w["scheme"])
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32_ir"])
+@pytest.mark.parametrize("n", [1, 7, 63, 1023, 4095])
+def test_pcg_case1_matches_oracle(gpu, n, precision):
+    w = workloads.config1(n=n)
+    prob = oracle_problem_1d(w)
+    b = prob.c0 * w["b"]                  # the workload writes (I + dt h^-a (...)) u = b
+    P = oracle.Tau1D.for_problem(prob, shift=True)
+    ref = oracle.pcg(prob.matvec, b, Pinv=P.apply_inverse, tol=1e-8)
+    tight = oracle.pcg(prob.matvec, b, Pinv=P.apply_inverse, tol=1e-13, maxiter=500)
+    plan = fde.Plan.from_workload(w, precision=precision)
+    info = plan.solve(to_dev(gpu, b, "f64"), tol=1e-8, inner_tol=1e-5)
+    x = info["x"].cpu().numpy()
+    assert info["status"] == fde.OK, info
+    if precision == "f64":
+        assert abs(info["iterations"] - ref.iterations) <= 1, (info, ref.iterations)
+    assert info["relres"] <= 1e-8
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+    info2 = plan.solve(to_dev(gpu, b, "f64"), tol=1e-13, max_iters=500, inner_tol=1e-5)
+    assert rel_err(info2["x"].cpu().numpy(), tight.x) < 1e-8
+
+
+@pytest.mark.parametrize("alpha", [1.2, 1.8])
+@pytest.mark.parametrize("n", [63, 1023, 4095, 16383])
+def test_gmres_right_variable_coefficients(gpu, n, alpha):
+    w = workloads.config2(n=n, alphas=(alpha,))[0]
+    prob = oracle_problem_1d(w)
+    b = prob.c0 * w["u0"]
+    P = oracle.Tau1D.for_problem(prob)
+    ref = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, x0=w["u0"], restart=30, tol=1e-8)
+    plan = fde.Plan.from_workload(w)
+    info = plan.solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8)
+    assert info["status"] == fde.OK, info
+    assert abs(info["iterations"] - ref.iterations) <= 1, (info, ref.iterations)
+    x = info["x"].cpu().numpy()
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+    tight = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, restart=30, tol=1e-12, maxiter=3000)
+    info2 = plan.solve(to_dev(gpu, b, "f64"), tol=1e-12, max_iters=3000)
+    assert rel_err(info2["x"].cpu().numpy(), tight.x) < 1e-8
+
+
+@pytest.mark.parametrize("precision,tol", [("f32", 1e-6), ("f32_ir", 1e-8)])
+@pytest.mark.parametrize("alpha", [1.2, 1.5])
+def test_gmres_mixed_precision(gpu, alpha, precision, tol):
+    n = 4095
+    w = workloads.config2(n=n, alphas=(alpha,))[0]
+    prob = oracle_problem_1d(w)
+    b = prob.c0 * w["u0"]
+    P = oracle.Tau1D.for_problem(prob)
+    tight = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, restart=30, tol=1e-12, maxiter=3000)
+    plan = fde.Plan.from_workload(w, precision=precision)
+    info = plan.solve(to_dev(gpu, b, "f64"), tol=tol if precision == "f32_ir" else 1e-6, inner_tol=1e-4,
+                      max_iters=3000)
+    x = info["x"].cpu().numpy()
+    relres = np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b)
+    if precision == "f32_ir":
+        assert info["status"] == fde.OK, info
+        assert relres <= 1.01e-8 and info["relres"] <= 1e-8
+        # one more solve to 1e-12 pins the refined solution
+        info2 = plan.solve(to_dev(gpu, b, "f64"), tol=1e-12, inner_tol=1e-4, max_iters=5000)
+        assert rel_err(info2["x"].cpu().numpy(), tight.x) < 1e-8
+    else:
+        assert relres <= 2e-6, (relres, info)
+        assert abs(info["relres"] - relres) <= 1e-3 * relres + 1e-12
+
+
+@pytest.mark.parametrize("n", [63, 255])
+def test_gmres_left_paper_mode_example1(gpu, n):
+    """Sec. 4 convention: left preconditioning, GMRES(20), x0 = 0, tol 1e-7."""
+    from oracle.examples import example1_problem, example1_source, example1_exact
+    prob, meta = example1_problem(1.5, n)
+    x = meta["x"]
+    plan = fde.Plan(1, n, 1.5, meta["ht"], len1=2.0, dp=prob.dp, dm=prob.dm, restart=20)
+    P = oracle.Tau1D.for_problem(prob)
+    u = example1_exact(x, 0.0)
+    for m in range(1, 4):
+        b = prob.c0 * u + meta["h"] ** 1.5 * example1_source(1.5, x, m * meta["ht"])
+        ref = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, side="left", restart=20, tol=1e-7)
+        info = plan.solve(to_dev(gpu, b, "f64"), tol=1e-7, side="left")
+        assert abs(info["iterations"] - ref.iterations) <= 1, (m, info, ref.iterations)
+        assert rel_err(info["x"].cpu().numpy(), ref.x) < 1e-6
+        u = ref.x
+
+
+def test_batched_case1_instances(gpu):
+    ws = workloads.config4(count=24, kmin=8, kmax=11)
+    plans, bs, xs, refs = [], [], [], []
+    for w in ws:
+        prob = oracle_problem_1d(w)
+        b = prob.c0 * w["b"]
+        P = oracle.Tau1D.for_problem(prob, shift=True)
+        refs.append((prob, b, oracle.pcg(prob.matvec, b, Pinv=P.apply_inverse, tol=1e-8)))
+        plans.append(fde.Plan.from_workload(w, precision="f32_ir"))
+        bs.append(to_dev(gpu, b, "f64"))
+        xs.append(gpu.zeros_like(bs[-1]))
+    infos = fde.solve_batch(plans, bs, xs, tol=1e-8, inner_tol=1e-5)
+    for (prob, b, ref), info, x in zip(refs, infos, xs):
+        assert info["status"] == fde.OK, info
+        xx = x.cpu().numpy()
+        assert np.linalg.norm(b - prob.matvec(xx)) / np.linalg.norm(b) <= 1.01e-8
+        assert rel_err(xx, ref.x) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32_ir"])
+@pytest.mark.parametrize("n", [63, 255])
+def test_2d_pcg_shifted(gpu, n, precision):
+    w = workloads.config3(n=n)
+    h = 1.0 / (n + 1)
+    prob = oracle.Problem2D(alpha=w["alpha"], beta=w["beta"], n1=n, n2=n, c0=h ** w["alpha"] / w["dt"],
+                            sr=h ** w["alpha"] / h ** w["beta"], dp=w["dp"], dm=w["dm"], ep=w["ep"], em=w["em"],
+                            scheme="wsgd2")
+    b = prob.c0 * w["b"]
+    P = oracle.Tau2D.for_problem(prob, shift=True)
+    ref = oracle.pcg(prob.matvec, b, Pinv=P.apply_inverse, tol=1e-8)
+    plan = fde.Plan.from_workload(w, precision=precision)
+    info = plan.solve(to_dev(gpu, b, "f64"), tol=1e-8, inner_tol=1e-5)
+    assert info["status"] == fde.OK, info
+    if precision == "f64":
+        assert abs(info["iterations"] - ref.iterations) <= 1, (info, ref.iterations)
+    x = info["x"].cpu().numpy()
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+    assert rel_err(x, ref.x) < 1e-6
+
+
+@pytest.mark.parametrize("n", [31, 127])
+def test_2d_gmres_variable(gpu, n):
+    w = workloads.config5(n=n)
+    h = 1.0 / (n + 1)
+    prob = oracle.Problem2D(alpha=w["alpha"], beta=w["beta"], n1=n, n2=n, c0=h ** w["alpha"] / w["dt"],
+                            sr=h ** w["alpha"] / h ** w["beta"], dp=w["dp"], dm=w["dm"], ep=w["ep"], em=w["em"],
+                            scheme="wsgd2")
+    b = prob.c0 * w["u0"]
+    P = oracle.Tau2D.for_problem(prob)
+    ref = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, x0=w["u0"], restart=20, tol=1e-8)
+    plan = fde.Plan.from_workload(w)
+    info = plan.solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8)
+    assert info["status"] == fde.OK, info
+    assert abs(info["iterations"] - ref.iterations) <= 1, (info, ref.iterations)
+    x = info["x"].cpu().numpy()
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+
+
+def test_zero_rhs_and_iteration_cap(gpu):
+    n = 255
+    plan, prob = make_1d(gpu, n, "var")
+    z = gpu.zeros(n, dtype=gpu.float64, device="cuda")
+    info = plan.solve(z, x=gpu.ones(n, dtype=gpu.float64, device="cuda"))
+    assert info["status"] == fde.OK and float(info["x"].abs().max()) == 0.0
+    b = to_dev(gpu, np.random.default_rng(0).uniform(-1, 1, n), "f64")
+    info = plan.solve(b, max_iters=2, tol=1e-12)
+    assert info["status"] == fde.ENOCONV and info["iterations"] == 2
+    assert 0 < info["relres"] < 1
+
+
+def test_full_size_variable_coefficient_step(gpu):
+    """One implicit-Euler step of the n = 65535 workload (alpha = 1.8) on the
+    split-line path: device relres re-checked by the oracle's direct sums."""
+    w = workloads.config2(alphas=(1.8,))[0]
+    prob = oracle_problem_1d(w)
+    b = prob.c0 * w["u0"]
+    plan = fde.Plan.from_workload(w)
+    info = plan.solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8)
+    assert info["status"] == fde.OK, info
+    x = info["x"].cpu().numpy()
+    rr = np.linalg.norm(b - prob.matvec(x, "direct")) / np.linalg.norm(b)
+    assert rr <= 1.01e-8 and abs(rr - info["relres"]) <= 1e-3 * rr
+    assert info["iterations"] <= 25
