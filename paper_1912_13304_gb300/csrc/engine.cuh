@@ -56,7 +56,7 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
     long long lo, hi;
     team_range(t, N, lo, hi);
     if constexpr (MODE == kModeF64) {
-        SolveParams sp{a.tol, a.max_iters, a.side};
+        SolveParams sp{a.tol, a.max_iters, a.side, 0};
         if (!krylov_core<double>(t, I, lm_f64(I), b, x, sp, st, ks, work, bytes)) return false;
     } else {
         float* rhs32 = reinterpret_cast<float*>(I.wvec) + extra_vec_offset<float>(I);
@@ -72,13 +72,14 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
                 sol32[i] = float(x[i]);
             }
             if (!team_sync(t)) return false;
-            SolveParams sp{a.tol, a.max_iters, a.side};
+            SolveParams sp{a.tol, a.max_iters, a.side, 1};
             if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, st, ks, work, bytes)) return false;
             for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) x[i] = double(sol32[i]);
             if (!team_sync(t)) return false;
             double rn;
             if (!residual64(t, I, b, x, ks, work, bytes, rn)) return false;
             st.relres = nb > 0.0 ? rn / nb : 0.0;
+            if (st.status == FDE_OK && !(st.relres <= a.tol)) st.status = FDE_ENOCONV;
         } else {
             int status = FDE_ENOCONV;
             int inner_status = FDE_OK;
@@ -98,7 +99,7 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
                 if (!team_sync(t)) return false;
                 SolveState in{};
                 in.iterations = st.iterations;
-                SolveParams sp{a.inner_tol, a.max_iters, a.side};
+                SolveParams sp{a.inner_tol, a.max_iters, a.side, 1};
                 if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, in, ks, work, bytes)) return false;
                 st.iterations = in.iterations;
                 st.restarts += in.restarts;

@@ -15,6 +15,7 @@ struct SolveParams {
     double tol;            // relative to ||rhs||
     int max_iters;         // cap on products with M
     int side;              // FDE_SIDE_RIGHT / FDE_SIDE_LEFT
+    int inner;             // inner solve of a refinement: stop on the Krylov estimate, no FP32 true residual
 };
 
 struct SolveState {
@@ -292,8 +293,13 @@ FDE_NI bool gmres_core(const Team& t, const Inst& I, int lm, const W* rhs, W* so
         const W* upd = left ? v.tt : v.z;
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sol[i] = sol[i] + ldw(upd + i);
         if (!team_sync(t)) return false;
+        // An inner solve trusts its estimate: below the working precision's
+        // floor a recomputed residual says nothing the outer FP64 residual won't.
+        if (sp.inner && (cycle_converged || st.iterations >= sp.max_iters)) {
+            st.status = cycle_converged ? FDE_OK : FDE_ENOCONV;
+            break;
+        }
         st.restarts++;
-        (void)cycle_converged;
         // loop: the true residual at the top decides
     }
     return team_sync(t);
@@ -382,6 +388,10 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
         rz = rz_new;
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) p[i] = W((double)ldw(z + i) + be * (double)ldw(p + i));
         if (!team_sync(t)) return false;
+    }
+    if (sp.inner) {
+        st.relres = st.relres_est;
+        return team_sync(t);
     }
     // true residual of the final iterate
     if (!op_matvec<W>(t, I, lm, sol, W(1), q, tt, work, bytes)) return false;
