@@ -316,17 +316,32 @@ __global__ void k_step_rhs(long long N, double c0, double ha, const double* u, c
 template <typename T>
 T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + off); }
 
+// Largest FFT a CTA runs for this problem, capped for the shared twiddle table.
+int twiddle_log(const fde_problem* p, const Layout& Lo, int line_mode64, int line_mode32) {
+    int lg = 2;
+    if (p->dim == 2) {
+        lg = std::max(ilog2(Lo.Np[0]), ilog2(Lo.Np[1]));
+    } else {
+        const int logNp = ilog2(Lo.Np[0]);
+        const int logP2 = logNp - logNp / 2;
+        const bool any_cta = line_mode64 == kLineCta || line_mode32 == kLineCta;
+        lg = any_cta ? logNp : logP2;
+    }
+    if (lg > kMaxLogTsm) lg = kMaxLogTsm;
+    return lg < 2 ? 2 : lg;
+}
+
 int line_modes(const fde_problem* p, const Layout& Lo, int work_bytes) {
     if (p->dim == 2) return kPlane | (kPlane << 8);
     const int Np = Lo.Np[0];
     const bool sym = p->dp == p->dm && (p->dp != nullptr || p->dp_const == p->dm_const);
     const int nbuf = sym ? 1 : 2;
-    auto fits = [&](int ept, int esz) {
-        return Np * nbuf <= ept * kThreads && (long long)Np * nbuf * esz <= work_bytes &&
-               (long long)Np * esz <= work_bytes;
+    // a whole line in one CTA: one FFT item per thread and the buffers in shared memory
+    auto fits = [&](int esz) {
+        return fft_items_per_line(ilog2(Np)) <= kThreads && (long long)padded_len(Np * nbuf) * esz <= work_bytes;
     };
-    const int m64 = fits(Ept<double>::v, (int)sizeof(cx<double>)) ? kLineCta : kLineSplit;
-    const int m32 = fits(Ept<float>::v, (int)sizeof(cx<float>)) ? kLineCta : kLineSplit;
+    const int m64 = fits((int)sizeof(cx<double>)) ? kLineCta : kLineSplit;
+    const int m32 = fits((int)sizeof(cx<float>)) ? kLineCta : kLineSplit;
     return m64 | (m32 << 8);
 }
 
@@ -398,7 +413,8 @@ fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* op
     for (int i = 0; i < 3; ++i) p->grid[i] = di->grid[i];
 
     const int m = opts->method == FDE_GMRES ? opts->restart : 1;
-    const int work_bytes = di->smem_bytes - (int)kshared_bytes(m);
+    // line modes against the shared memory left beside the largest twiddle table
+    const int work_bytes = di->smem_bytes - (int)kshared_bytes(m, kMaxLogTsm);
 
     Inst& I = p->inst;
     std::memset(&I, 0, sizeof(Inst));
@@ -426,6 +442,7 @@ fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* op
         I.phi_scale2d = 1.0 / ((double)(prob->n1 + 1) * (double)(prob->n2 + 1));
     }
     I.logTW = Lo.logTW;
+    I.logTsm = twiddle_log(prob, Lo, I.line_mode & 0xff, (I.line_mode >> 8) & 0xff);
     I.tw64 = at<cx<double>>(workspace, Lo.tw64);
     I.tw32 = at<cx<float>>(workspace, Lo.tw32);
     for (int a = 0; a < prob->dim; ++a) {

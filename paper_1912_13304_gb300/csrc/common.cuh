@@ -19,6 +19,8 @@ constexpr int kMaxRestart = 64;        // GMRES(m) upper bound on m
 constexpr int kMaxDots = kMaxRestart + 2;
 constexpr int kMaxBatch = 1024;        // instances per fde_krylov_solve launch
 constexpr int kMaxCtas = 1024;         // grid-size bound for the sync region
+constexpr int kTraceEntries = 8192;    // phase timestamps of FDE_TRACE builds
+constexpr int kMaxLogTsm = 12;         // shared twiddle table: up to W_4096 (16 KB quarter wave)
 
 template <typename R>
 struct alignas(2 * sizeof(R)) cx {
@@ -68,6 +70,7 @@ struct Inst {
     double phi_scale2d;                // 2/(n1+1) / L2 folded into the 2D tau multiplier
     AxisData ax[2];
     int logTW;
+    int logTsm;                        // shared-memory twiddle table covers FFTs up to 2^logTsm
     const cx<double>* tw64;            // [TW] exp(-2 pi i t / TW)
     const cx<float>* tw32;
     // diffusion coefficients: arrays (FP64 user memory, FP32 copies) or constants
@@ -90,8 +93,10 @@ struct SyncArea {
     unsigned int bar_gen[kMaxCtas];
     unsigned int queue;                // dynamic instance queue for one-CTA teams
     unsigned int abort_flag;
-    unsigned int pad[62];
+    unsigned int trace_n;              // FDE_TRACE builds: entries written to trace[]
+    unsigned int pad[61];
     double partial[kMaxCtas * kMaxDots];
+    unsigned long long trace[kTraceEntries];   // (code << 48) | globaltimer ns
 };
 
 template <typename W> struct Prec;

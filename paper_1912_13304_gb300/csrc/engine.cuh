@@ -32,12 +32,10 @@ FDE_D int lm_f32(const Inst& I) { return (I.line_mode >> 8) & 0xff; }
 
 // FP64 residual r64 = b - A x and its norm (refinement and FP32 modes).
 static FDE_NI bool residual64(const Team& t, const Inst& I, const double* b, const double* x, KShared& ks,
-                      unsigned char* work, int bytes, double& rn) {
-    if (!op_matvec<double>(t, I, lm_f64(I), x, 1.0, I.t64, I.r64, work, bytes)) return false;
-    long long lo, hi;
-    team_range(t, I.N, lo, hi);
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) I.r64[i] = __ldcg(b + i) - __ldcg(I.t64 + i);
-    if (!team_sync(t)) return false;
+                              const Wk& wk, double& rn) {
+    // r64 = b - A x, written by the matvec's epilogue (t64 is the 2D scratch)
+    if (!op_matvec_out<double>(t, I, lm_f64(I), x, 1.0, I.t64, OutSpec<double>{kOutResid, I.r64, b}, wk))
+        return false;
     const double* a[1] = {I.r64};
     if (!dots_pairs<double, 1>(t, I.N, a, a, ks)) return false;
     rn = sqrt(ks.red[0]);
@@ -45,8 +43,7 @@ static FDE_NI bool residual64(const Team& t, const Inst& I, const double* b, con
 }
 
 template <int MODE>
-FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx, KShared& ks, unsigned char* work,
-                     int bytes) {
+FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx, KShared& ks, const Wk& wk) {
     const double* b = reinterpret_cast<const double*>(a.in[idx]);
     double* x = reinterpret_cast<double*>(a.out[idx]);
     SolveState st{};
@@ -57,7 +54,7 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
     team_range(t, N, lo, hi);
     if constexpr (MODE == kModeF64) {
         SolveParams sp{a.tol, a.max_iters, a.side, 0};
-        if (!krylov_core<double>(t, I, lm_f64(I), b, x, sp, st, ks, work, bytes)) return false;
+        if (!krylov_core<double>(t, I, lm_f64(I), b, x, sp, st, ks, wk)) return false;
     } else {
         float* rhs32 = reinterpret_cast<float*>(I.wvec) + extra_vec_offset<float>(I);
         float* sol32 = rhs32 + N;
@@ -73,11 +70,11 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
             }
             if (!team_sync(t)) return false;
             SolveParams sp{a.tol, a.max_iters, a.side, 1};
-            if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, st, ks, work, bytes)) return false;
+            if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, st, ks, wk)) return false;
             for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) x[i] = double(sol32[i]);
             if (!team_sync(t)) return false;
             double rn;
-            if (!residual64(t, I, b, x, ks, work, bytes, rn)) return false;
+            if (!residual64(t, I, b, x, ks, wk, rn)) return false;
             st.relres = nb > 0.0 ? rn / nb : 0.0;
             if (st.status == FDE_OK && !(st.relres <= a.tol)) st.status = FDE_ENOCONV;
         } else {
@@ -85,7 +82,7 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
             int inner_status = FDE_OK;
             while (true) {
                 double rn;
-                if (!residual64(t, I, b, x, ks, work, bytes, rn)) return false;
+                if (!residual64(t, I, b, x, ks, wk, rn)) return false;
                 st.relres = nb > 0.0 ? rn / nb : 0.0;
                 if (!finite(rn)) { status = FDE_ENONFINITE; break; }
                 if (rn <= a.tol * nb) { status = FDE_OK; break; }
@@ -100,7 +97,7 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
                 SolveState in{};
                 in.iterations = st.iterations;
                 SolveParams sp{a.inner_tol, a.max_iters, a.side, 1};
-                if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, in, ks, work, bytes)) return false;
+                if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, in, ks, wk)) return false;
                 st.iterations = in.iterations;
                 st.restarts += in.restarts;
                 st.relres_est = in.relres_est;
@@ -126,20 +123,20 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
 }
 
 template <int MODE>
-FDE_D bool run_op(const Team& t, const Inst& I, const EngineArgs& a, int idx, unsigned char* work, int bytes) {
+FDE_D bool run_op(const Team& t, const Inst& I, const EngineArgs& a, int idx, const Wk& wk) {
     const bool f64 = (MODE == kModeF64) || a.dtype == FDE_F64;
     if (f64) {
         const double* in = reinterpret_cast<const double*>(a.in[idx]);
         double* out = reinterpret_cast<double*>(a.out[idx]);
-        if (a.op == kOpMatvec) return op_matvec<double>(t, I, lm_f64(I), in, 1.0, out, I.t64, work, bytes);
-        return op_tau<double>(t, I, lm_f64(I), in, 1.0, out, work, bytes);
+        if (a.op == kOpMatvec) return op_matvec<double>(t, I, lm_f64(I), in, 1.0, out, I.t64, wk);
+        return op_tau<double>(t, I, lm_f64(I), in, 1.0, out, wk);
     }
     if constexpr (MODE != kModeF64) {
         const float* in = reinterpret_cast<const float*>(a.in[idx]);
         float* out = reinterpret_cast<float*>(a.out[idx]);
         float* tmp = reinterpret_cast<float*>(I.t64);
-        if (a.op == kOpMatvec) return op_matvec<float>(t, I, lm_f32(I), in, 1.0f, out, tmp, work, bytes);
-        return op_tau<float>(t, I, lm_f32(I), in, 1.0f, out, work, bytes);
+        if (a.op == kOpMatvec) return op_matvec<float>(t, I, lm_f32(I), in, 1.0f, out, tmp, wk);
+        return op_tau<float>(t, I, lm_f32(I), in, 1.0f, out, wk);
     }
     return true;
 }
@@ -160,6 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
     t.gen = &a.sync->bar_gen[team_id];
     t.partial = a.sync->partial + (size_t)team_id * ts * kMaxDots;
     t.abort_flag = &a.sync->abort_flag;
+    t.sync = a.sync;
     int next_static = team_id;
     while (true) {
         int idx;
@@ -182,13 +180,32 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
         }
         __syncthreads();
         const int m = s_inst.method == FDE_GMRES ? s_inst.restart : 1;
-        const size_t hdr = kshared_bytes(m);
+        const size_t hdr = kshared_bytes(m, s_inst.logTsm);
         KShared ks = kshared_carve(dsm, m);
-        unsigned char* work = dsm + hdr;
-        const int bytes = a.smem_bytes - (int)hdr;
+        // quarter-wave twiddle table of W_T, T = 2^logTsm, from the global table
+        {
+            const int q = (1 << s_inst.logTsm) >> 2;
+            const int sh = s_inst.logTW - s_inst.logTsm;
+            ks.twq32 = reinterpret_cast<cx<float>*>(ks.twq + q);
+            for (int i = threadIdx.x; i < q; i += blockDim.x) {
+                const cx<double> w = s_inst.tw64[i << sh];
+                ks.twq[i] = w;
+                ks.twq32[i] = mk((float)w.x, (float)w.y);
+            }
+        }
+        __syncthreads();
+        Wk wk;
+        wk.smem = dsm + hdr;
+        wk.bytes = a.smem_bytes - (int)hdr;
+        wk.tw.q = ks.twq;
+        wk.tw.q32 = ks.twq32;
+        wk.tw.logT = s_inst.logTsm;
+        wk.tw.g64 = s_inst.tw64;
+        wk.tw.g32 = s_inst.tw32;
+        wk.tw.logTW = s_inst.logTW;
         bool ok;
-        if (a.op == kOpSolve) ok = run_solve<MODE>(t, s_inst, a, inst_i, ks, work, bytes);
-        else ok = run_op<MODE>(t, s_inst, a, inst_i, work, bytes);
+        if (a.op == kOpSolve) ok = run_solve<MODE>(t, s_inst, a, inst_i, ks, wk);
+        else ok = run_op<MODE>(t, s_inst, a, inst_i, wk);
         if (!ok) {
             if (threadIdx.x == 0 && t.rank == 0 && a.op == kOpSolve) {
                 a.info[inst_i].status = FDE_ETIMEOUT;

@@ -1,17 +1,62 @@
 // Power-of-two complex FFTs for one CTA: Stockham autosort radix-8/4/2 passes
-// whose butterflies run in registers.  Data may sit in shared memory
-// (in place: every thread stages its inputs in registers, the CTA
-// synchronises, then writes) or in global memory (ping-pong between two
-// buffers, used only by the one-time symbol assembly).
+// whose butterflies run in registers.  Data sit in shared memory (in place:
+// every thread stages its inputs in registers, the CTA synchronises, then
+// writes) or, for the one-time symbol assembly, in global memory (ping-pong).
+//
+// Shared-memory line buffers are indexed through pad(i) = i + i/16: one
+// spare complex every 16 keeps every Stockham read and write pattern at the
+// minimum number of bank wavefronts (the radix-8 first pass writes at stride
+// 8 and would otherwise be 8- to 16-way conflicted).
 //
 // Conventions: forward X_j = sum_k x_k w^{jk}, w = exp(-2 pi i / P); inverse
-// uses w^{-1} and is unnormalised.  Twiddles come from a table
-// tw[t] = exp(-2 pi i t / TW), TW a power of two >= P.
+// uses w^{-1} and is unnormalised.  Radix twiddles come from a quarter-wave
+// FP64 table of W_T in shared memory when P <= T, else from the global
+// table of W_TW.
 #pragma once
 
 #include "common.cuh"
 
 namespace fde {
+
+FDE_HD int pad(int i) { return i + (i >> 4); }
+FDE_HD int padded_len(int n) { return n + (n >> 4) + 1; }
+
+// Twiddle sources of one CTA.
+struct Tw {
+    const cx<double>* q;       // shared memory: W_T^t for t < T/4 (quarter wave)
+    const cx<float>* q32;      // the same table rounded to FP32
+    int logT;
+    const cx<double>* g64;     // global: W_TW^t for t < TW
+    const cx<float>* g32;
+    int logTW;
+};
+
+template <typename R> FDE_D const cx<R>* tw_global_table(const Tw& t);
+template <> FDE_D const cx<double>* tw_global_table<double>(const Tw& t) { return t.g64; }
+template <> FDE_D const cx<float>* tw_global_table<float>(const Tw& t) { return t.g32; }
+
+// W_T^idx (idx < T) from the quarter table: W^{q T/4 + r} = (-i)^q W^r.
+template <typename R> FDE_D cx<R> tw_quarter_entry(const Tw& t, int r);
+template <> FDE_D cx<double> tw_quarter_entry<double>(const Tw& t, int r) { return t.q[r]; }
+template <> FDE_D cx<float> tw_quarter_entry<float>(const Tw& t, int r) { return t.q32[r]; }
+
+// Branch-free: quadrants 1 and 3 swap the components, the first component is
+// negated in quadrants 2 and 3, the second in quadrants 1 and 2.
+template <typename R>
+FDE_D cx<R> tw_quarter(const Tw& t, int idx) {
+    const int q = (idx >> (t.logT - 2)) & 3;
+    const int r = idx & ((1 << (t.logT - 2)) - 1);
+    const cx<R> w = tw_quarter_entry<R>(t, r);
+    const R a = (q & 1) ? w.y : w.x;
+    const R b = (q & 1) ? w.x : w.y;
+    return mk((q & 2) ? -a : a, ((q + 1) & 2) ? -b : b);
+}
+
+// W_L^j for the real-packing step (L = 2^logL, any size): global table.
+template <typename R>
+FDE_D cx<R> tw_L(const Tw& t, long long j, int logL) {
+    return tw_global_table<R>(t)[j << (t.logTW - logL)];
+}
 
 // ---------------------------------------------------------------------------
 // Register DFTs
@@ -70,77 +115,104 @@ FDE_D void dft_reg(cx<R>* v) {
     else dft8<R, INV>(v);
 }
 
-template <typename R, bool INV>
-FDE_D cx<R> twiddle(const cx<R>* tw, int idx) {
-    cx<R> w = tw[idx];
-    return INV ? conj(w) : w;
-}
-
 // ---------------------------------------------------------------------------
 // One Stockham pass over `nlines` lines of length P (= 2^logP) at stride
-// `lstride`.  Item j of a line reads x[j + r P/RAD], applies the twiddles
-// w_{Ns RAD}^{r k} (k = j mod Ns), a radix-RAD DFT, and writes
-// y[(j - k) RAD + k + r Ns].
+// `lstride` (flat, unpadded indices).  Item j of a line reads x[j + r P/RAD],
+// applies the twiddles w_{Ns RAD}^{r k} (k = j mod Ns), a radix-RAD DFT, and
+// writes y[(j - k) RAD + k + r Ns].
 // ---------------------------------------------------------------------------
 
 template <typename R, int RAD, int EPT, bool INV>
-FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, int logNs,
-                                 const cx<R>* tw, int logTW) {
+FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, int logNs, const Tw& tw,
+                                 bool smem_tw) {
     constexpr int K = EPT / RAD;                // items per thread
     constexpr int LR = RAD == 8 ? 3 : (RAD == 4 ? 2 : 1);
     const int logItems = logP - LR;             // items per line = P / RAD
     const int total = nlines << logItems;
     const int Ns = 1 << logNs;
-    const int twsh = logTW - logNs - LR;        // table step for w_{Ns RAD}
+    const int twsh = (smem_tw ? tw.logT : tw.logTW) - logNs - LR;
+    const cx<R>* gtab = tw_global_table<R>(tw);
     cx<R> v[K][RAD];
-    int dst[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
         const int it = threadIdx.x + t * blockDim.x;
-        dst[t] = -1;
         if (it < total) {
             const int line = it >> logItems;
             const int j = it & ((1 << logItems) - 1);
-            cx<R>* base = buf + (long long)line * lstride;
+            const int base = line * lstride;
             const int k = j & (Ns - 1);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) v[t][r] = base[j + (r << logItems)];
+            for (int r = 0; r < RAD; ++r) v[t][r] = buf[pad(base + j + (r << logItems))];
             if (Ns > 1) {
 #pragma unroll
-                for (int r = 1; r < RAD; ++r) v[t][r] = v[t][r] * twiddle<R, INV>(tw, (r * k) << twsh);
+                for (int r = 1; r < RAD; ++r) {
+                    const int idx = (r * k) << twsh;
+                    cx<R> w = smem_tw ? tw_quarter<R>(tw, idx) : gtab[idx];
+                    if (INV) w = conj(w);
+                    v[t][r] = v[t][r] * w;
+                }
             }
             dft_reg<R, RAD, INV>(v[t]);
-            dst[t] = line * lstride + (j - k) * RAD + k;
         }
     }
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        if (dst[t] >= 0) {
+        const int it = threadIdx.x + t * blockDim.x;
+        if (it < total) {
+            const int line = it >> logItems;
+            const int j = it & ((1 << logItems) - 1);
+            const int k = j & (Ns - 1);
+            const int dst = line * lstride + (j - k) * RAD + k;
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) buf[dst[t] + r * Ns] = v[t][r];
+            for (int r = 0; r < RAD; ++r) buf[pad(dst + r * Ns)] = v[t][r];
         }
     }
     __syncthreads();
 }
 
-// In-place FFT of nlines lines held in shared memory.  Requires
-// nlines * P <= EPT * blockDim.x (every element staged in registers once).
-template <typename R, int EPT, bool INV>
-FDE_NI void fft_inplace(cx<R>* buf, int logP, int nlines, int lstride, const cx<R>* tw, int logTW) {
+// In-place FFT of nlines lines held in (padded) shared memory, every pass
+// one radix item per thread (registers hold RAD values), so a call requires
+// nlines * P / RAD <= blockDim.x for the smallest radix it uses.
+template <typename R, bool INV>
+FDE_D void fft_inplace(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
+    const bool smem_tw = logP <= tw.logT;
     int logNs = 0;
     int rem = logP;
     while (rem >= 3) {
-        stockham_pass_inplace<R, 8, EPT, INV>(buf, logP, nlines, lstride, logNs, tw, logTW);
+        stockham_pass_inplace<R, 8, 8, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
         logNs += 3;
         rem -= 3;
     }
-    if (rem == 2) stockham_pass_inplace<R, 4, EPT, INV>(buf, logP, nlines, lstride, logNs, tw, logTW);
-    else if (rem == 1) stockham_pass_inplace<R, 2, EPT, INV>(buf, logP, nlines, lstride, logNs, tw, logTW);
+    if (rem == 2) stockham_pass_inplace<R, 4, 4, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+    else if (rem == 1) stockham_pass_inplace<R, 2, 2, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
 }
 
-// Ping-pong variant for one long line in global memory (one CTA).  Returns the
-// buffer that holds the result.
+// Radix items per line of the widest pass (the last one, whose radix is the
+// smallest), and the lines one call of fft_inplace can take.
+FDE_HD int fft_items_per_line(int logP) {
+    const int r = logP % 3;
+    const int last = r == 0 ? 3 : r;
+    return logP >= last ? 1 << (logP - last) : 1;
+}
+FDE_HD int fft_lines_per_call(int logP, int threads) { return threads / fft_items_per_line(logP); }
+
+// FFT of nlines lines of 2^logP at stride lstride (flat index), in batches
+// of lines; the flat origin of a batch starting at line l0 is pad(l0 *
+// lstride), which commutes with pad() because lstride is a multiple of 16
+// whenever more than one batch is needed.  A single line longer than the CTA
+// covers one item per thread is not supported (callers split such lines).
+template <typename R, bool INV>
+FDE_D void fft_lines(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
+    const int cap = fft_lines_per_call(logP, blockDim.x);
+    for (int l0 = 0; l0 < nlines; l0 += cap) {
+        const int nl = (nlines - l0) < cap ? (nlines - l0) : cap;
+        fft_inplace<R, INV>(buf + pad(l0 * lstride), logP, nl, lstride, tw);
+    }
+}
+
+// Ping-pong variant for one long line in global memory (one CTA, symbol
+// assembly only).  Returns the buffer that holds the result.
 template <typename R, int RAD, bool INV>
 FDE_D void stockham_pass_pp(const cx<R>* src, cx<R>* dst, int logP, int logNs, const cx<R>* tw,
                             int logTW) {
@@ -156,7 +228,11 @@ FDE_D void stockham_pass_pp(const cx<R>* src, cx<R>* dst, int logP, int logNs, c
         for (int r = 0; r < RAD; ++r) v[r] = src[j + (r << logItems)];
         if (Ns > 1) {
 #pragma unroll
-            for (int r = 1; r < RAD; ++r) v[r] = v[r] * twiddle<R, INV>(tw, (r * k) << twsh);
+            for (int r = 1; r < RAD; ++r) {
+                cx<R> w = tw[(r * k) << twsh];
+                if (INV) w = conj(w);
+                v[r] = v[r] * w;
+            }
         }
         dft_reg<R, RAD, INV>(v);
         const int d = (j - k) * RAD + k;

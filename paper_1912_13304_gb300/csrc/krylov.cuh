@@ -1,10 +1,20 @@
 // Device-resident Krylov drivers: PCG and restarted GMRES(m) (right or left
-// preconditioned, classical Gram-Schmidt with one reorthogonalisation), and
-// the FP32-inner / FP64-outer iterative refinement around them.  Every CTA of
-// a team runs the same scalar recurrences on the same deterministic
-// reductions, so all CTAs take identical decisions without extra barriers.
-// Inner products, norms, the Hessenberg matrix and the Givens rotations are
-// FP64 whatever the vector precision.
+// preconditioned), and the FP32-inner / FP64-outer iterative refinement
+// around them.  Every CTA of a team runs the same scalar recurrences on the
+// same deterministic reductions, so all CTAs take identical decisions
+// without extra barriers.  Inner products, norms, the Hessenberg matrix and
+// the Givens rotations are FP64 whatever the vector precision.
+//
+// Right-preconditioned GMRES uses a fused Arnoldi step: the basis vector
+// v_j = w_{j-1} - sum_q c_q v_q is formed on the fly by the first transform
+// phase of the tau solve (and stored there), the tau solve hands z straight
+// to the matvec on the same CTAs where the layout allows, and the matvec's
+// last phase is followed by the partial inner products <w, v_i> and ||w||^2
+// of the elements the CTA produced -- one reduction per iteration.
+// Classical Gram-Schmidt is reorthogonalised (a second pass) only when the
+// projection leaves less than a tenth of ||w|| (a Daniel-Gragg-Kaufman-
+// Stewart test), so the common step needs no second reduction.  For FP32
+// vectors the inner products use compensated FP32 arithmetic (team.cuh).
 #pragma once
 
 #include "ops.cuh"
@@ -15,7 +25,7 @@ struct SolveParams {
     double tol;            // relative to ||rhs||
     int max_iters;         // cap on products with M
     int side;              // FDE_SIDE_RIGHT / FDE_SIDE_LEFT
-    int inner;             // inner solve of a refinement: stop on the Krylov estimate, no FP32 true residual
+    int inner;             // inner solve of a refinement: stop on the Krylov estimate
 };
 
 struct SolveState {
@@ -26,7 +36,8 @@ struct SolveState {
     double relres;         // true residual of the last check, relative to ||rhs||
 };
 
-// Shared-memory scalars of one CTA (identical in every CTA of a team).
+// Shared-memory scalars of one CTA (identical in every CTA of a team), and
+// the quarter-wave twiddle table.
 struct KShared {
     double* H;             // (m+1) x m, column-major H[i + j (m+1)]
     double* cs;
@@ -36,12 +47,33 @@ struct KShared {
     double* vs;            // 1/||v_i|| of the stored (unnormalised) basis vectors
     double* red;           // reduction results, kMaxDots + 8
     double* scratch;       // 8 * 32 for block_sum
-    double* coef;          // per-basis coefficients for fused updates
+    double* coef;          // coefficients of the next on-the-fly basis vector
+    float* coef32;         // the same, for FP32 vectors
+    cx<double>* twq;       // W_T^t, t < T/4
+    cx<float>* twq32;
 };
 
-FDE_HD size_t kshared_bytes(int m) {
-    size_t d = (size_t)(m + 1) * m + 3 * (size_t)m + 2 * (size_t)(m + 2) + (kMaxDots + 8) + 8 * 32 + (m + 2);
+// Coefficients in the working precision.
+template <typename W> FDE_D W* kcoef(KShared& ks);
+template <> FDE_D double* kcoef<double>(KShared& ks) { return ks.coef; }
+template <> FDE_D float* kcoef<float>(KShared& ks) { return ks.coef32; }
+// Thread 0 sets coefficient q in both precisions.
+FDE_D void set_coef(KShared& ks, int q, double v) {
+    ks.coef[q] = v;
+    ks.coef32[q] = (float)v;
+}
+
+FDE_HD size_t kshared_scalar_bytes(int m) {
+    const size_t d = (size_t)(m + 1) * m + 3 * (size_t)m + 2 * (size_t)(m + 2) + (kMaxDots + 8) + 8 * 32 +
+                     (kMaxDots + 2) + (kMaxDots + 2) / 2 + 1;
     return ((d * sizeof(double)) + 255) & ~(size_t)255;
+}
+
+// Rounded to 256 bytes: the transform buffers that follow need 16-byte
+// alignment whatever the table size.
+FDE_HD size_t kshared_bytes(int m, int logT) {
+    const size_t b = kshared_scalar_bytes(m) + (((size_t)1 << logT) / 4) * (sizeof(cx<double>) + sizeof(cx<float>));
+    return (b + 255) & ~(size_t)255;
 }
 
 FDE_D KShared kshared_carve(unsigned char* base, int m) {
@@ -55,7 +87,9 @@ FDE_D KShared kshared_carve(unsigned char* base, int m) {
     k.vs = p; p += m + 2;
     k.red = p; p += kMaxDots + 8;
     k.scratch = p; p += 8 * 32;
-    k.coef = p;
+    k.coef = p; p += kMaxDots + 2;
+    k.coef32 = reinterpret_cast<float*>(p);
+    k.twq = reinterpret_cast<cx<double>*>(base + kshared_scalar_bytes(m));
     return k;
 }
 
@@ -65,48 +99,149 @@ FDE_D bool finite(double v) { return isfinite(v); }
 // Reductions over N-vectors
 // ---------------------------------------------------------------------------
 
-// out[i] = <a, vs_i V_i> for i < cnt (V_i at V + i N); with `norm`, also
-// out[cnt] = <a, a>.  Team-wide totals in every CTA.
-template <typename W>
-FDE_D bool dots_basis(const Team& t, long long N, const W* a, const W* V, const double* vs, int cnt, bool norm,
-                      KShared& ks) {
-    long long lo, hi;
-    team_range(t, N, lo, hi);
+// ks.red[i] = <a, vs_i V_i> for i < cnt; with `norm`, ks.red[cnt] = <a, a>,
+// summed over the elements that own(f) visits (f(p) per element, threads of
+// this CTA), then over the team.
+template <typename W, typename OwnF>
+FDE_D bool dots_own(const Team& t, long long N, const W* a, const W* V, const double* vs, int cnt, bool norm,
+                    KShared& ks, OwnF own) {
     const int tot = cnt + (norm ? 1 : 0);
     for (int c0 = 0; c0 < tot; c0 += 8) {
-        double acc[8];
+        if constexpr (sizeof(W) == 8) {
+            double acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = 0.0;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const double ai = (double)ldw(a + i);
+            for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+            own([&](long long i) {
+                const double ai = (double)ldw(a + i);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int kk = c0 + k;
-                if (kk < cnt) acc[k] += ai * (double)ldw(V + (long long)kk * N + i);
-                else if (kk == cnt && norm) acc[k] += ai * ai;
-            }
+                for (int k = 0; k < 8; ++k) {
+                    const int kk = c0 + k;
+                    if (kk < cnt) acc[k] += ai * (double)ldw(V + (long long)kk * N + i);
+                    else if (kk == cnt && norm) acc[k] += ai * ai;
+                }
+            });
+            block_sum<8>(acc, ks.red + c0, ks.scratch);
+        } else {
+            F2 acc[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = F2{0.0f, 0.0f};
+            own([&](long long i) {
+                const float ai = (float)ldw(a + i);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int kk = c0 + k;
+                    if (kk < cnt) dot2_acc(acc[k], ai, (float)ldw(V + (long long)kk * N + i));
+                    else if (kk == cnt && norm) dot2_acc(acc[k], ai, ai);
+                }
+            });
+            block_sum_f2<8>(acc, ks.red + c0, ks.scratch);
         }
-        block_sum<8>(acc, ks.red + c0, ks.scratch);
     }
     if (threadIdx.x < cnt) ks.red[threadIdx.x] *= vs[threadIdx.x];
     __syncthreads();
     return team_allreduce(t, ks.red, tot);
 }
 
-// out[k] = <a_k, b_k> for up to 4 pairs (any pointer may repeat).
+template <typename W>
+FDE_D bool dots_basis(const Team& t, long long N, const W* a, const W* V, const double* vs, int cnt, bool norm,
+                      KShared& ks) {
+    long long lo, hi;
+    team_range(t, N, lo, hi);
+    return dots_own<W>(t, N, a, V, vs, cnt, norm, ks, [&](auto f) {
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) f(i);
+    });
+}
+
+// ks.red[k] = <a_k, b_k> for up to 8 pairs over the team partition.
 template <typename W, int K>
 FDE_D bool dots_pairs(const Team& t, long long N, const W* const (&a)[K], const W* const (&b)[K], KShared& ks) {
     long long lo, hi;
     team_range(t, N, lo, hi);
-    double acc[8];
+    if constexpr (sizeof(W) == 8) {
+        double acc[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.0;
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += (double)ldw(a[k] + i) * (double)ldw(b[k] + i);
+            for (int k = 0; k < K; ++k) acc[k] += (double)ldw(a[k] + i) * (double)ldw(b[k] + i);
+        }
+        block_sum<8>(acc, ks.red, ks.scratch);
+    } else {
+        F2 acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = F2{0.0f, 0.0f};
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) dot2_acc(acc[k], (float)ldw(a[k] + i), (float)ldw(b[k] + i));
+        }
+        block_sum_f2<8>(acc, ks.red, ks.scratch);
     }
-    block_sum<8>(acc, ks.red, ks.scratch);
     return team_allreduce(t, ks.red, K);
+}
+
+// ---------------------------------------------------------------------------
+// Fused right-preconditioned Arnoldi application:
+//   z = P^{-1} u, w = M z, ks.red[i] = <w, vs_i V_i> (i < nd), ks.red[nd] = ||w||^2.
+// ---------------------------------------------------------------------------
+
+template <typename W>
+FDE_NI bool arnoldi_right(const Team& t, const Inst& I, int lm, Combo<W> u, int nd, const W* V, W* z, W* w,
+                          W* tmp, KShared& ks, const Wk& wk) {
+    const long long N = I.N;
+    const W* dinv = Prec<W>::dinv(I);
+    const bool pre = I.has_D && I.order == FDE_ORDER_D_TAU;
+    trace_mark(t, 20);
+    if (I.dim == 1 && lm == kLineCta) {
+        // team of one: everything stays in this CTA
+        cta_tau_1d<W>(I, wk, u, epi_a<W>(nullptr, out_store<W>(z)));
+        cta_matvec_1d<W>(I, wk, z, W(1), epi_mvx<W>(I, z, W(1), out_store<W>(w)));
+        trace_mark(t, 13);
+        return dots_own<W>(t, N, w, V, ks.vs, nd, true, ks, [&](auto f) {
+            for (long long i = threadIdx.x; i < N; i += blockDim.x) f(i);
+        });
+    }
+    if (I.dim == 1) {
+        const AxisData& A = I.ax[0];
+        cx<W>* Y = Prec<W>::split(I);
+        cx<W>* Y2 = Y + A.Np;
+        const bool sym = I.symx;
+        if (pre) u.pre = dinv;
+        const int cc = split_cols_per_unit<W>(A, t.size, wk.bytes);
+        split_fwd_cols<W, kExtOdd>(t, I, wk, u, Y, cc);
+        if (!team_sync(t)) return false;
+        trace_mark(t, 21);
+        split_rows<W>(t, I, wk, mult_tau1<W>(A), Y, nullptr);
+        if (!team_sync(t)) return false;
+        trace_mark(t, 22);
+        split_tau_inv_mv_fwd<W>(t, I, wk, Y, Y, cc, z);
+        if (!team_sync(t)) return false;
+        trace_mark(t, 11);
+        split_rows<W>(t, I, wk, mult_matvec<W>(A, sym), Y, Y2);
+        if (!team_sync(t)) return false;
+        trace_mark(t, 12);
+        split_inv_cols<W>(t, I, wk, Y, Y2, cc, !sym, epi_mvx<W>(I, z, W(1), out_store<W>(w)));
+        trace_mark(t, 13);
+        const int units = A.P2 / cc;
+        return dots_own<W>(t, N, w, V, ks.vs, nd, true, ks, [&](auto f) {
+            for (int un = t.rank; un < units; un += t.size) split_unit_elements(A, un * cc, cc, f);
+        });
+    }
+    // 2D plane: rows (first sine transform) | columns (tau) | rows (second sine
+    // transform + x part of the matvec) | columns (y part) + dots
+    if (pre) u.pre = dinv;
+    plane_dst_rows<W>(t, I, wk, u, nullptr, z);
+    if (!team_sync(t)) return false;
+    trace_mark(t, 21);
+    plane_tau_cols<W>(t, I, wk, z);
+    if (!team_sync(t)) return false;
+    trace_mark(t, 22);
+    plane_dst_matvec_rows<W>(t, I, wk, z, z, tmp);
+    if (!team_sync(t)) return false;
+    trace_mark(t, 11);
+    plane_matvec_cols<W>(t, I, wk, z, W(1), epi_mvy<W>(I, tmp, out_store<W>(w)));
+    trace_mark(t, 13);
+    return dots_own<W>(t, N, w, V, ks.vs, nd, true, ks,
+                       [&](auto f) { plane_cols_own_elements<W>(t, I, wk.bytes, f); });
 }
 
 // ---------------------------------------------------------------------------
@@ -139,17 +274,41 @@ FDE_D long long extra_vec_offset(const Inst& I) {
     return I.method == FDE_GMRES ? (long long)(I.restart + 4) * I.N : 5LL * I.N;
 }
 
+// Givens rotation of Hessenberg column j (thread 0); updates g.
+FDE_D void givens_column(KShared& ks, int j, int m) {
+    double* Hc = ks.H + j * (m + 1);
+    for (int q = 0; q < j; ++q) {
+        const double a = ks.cs[q] * Hc[q] + ks.sn[q] * Hc[q + 1];
+        Hc[q + 1] = -ks.sn[q] * Hc[q] + ks.cs[q] * Hc[q + 1];
+        Hc[q] = a;
+    }
+    const double den = hypot(Hc[j], Hc[j + 1]);
+    ks.cs[j] = den > 0.0 ? Hc[j] / den : 1.0;
+    ks.sn[j] = den > 0.0 ? Hc[j + 1] / den : 0.0;
+    Hc[j] = den;
+    Hc[j + 1] = 0.0;
+    ks.g[j + 1] = -ks.sn[j] * ks.g[j];
+    ks.g[j] = ks.cs[j] * ks.g[j];
+}
+
+// y = H^{-1} g for the k x k triangle, then coef_i = sign y_i vs_i (thread 0).
+FDE_D void solve_triangle(KShared& ks, int k, int m, double sign) {
+    for (int i = k - 1; i >= 0; --i) {
+        double s = ks.g[i];
+        for (int q = i + 1; q < k; ++q) s -= ks.H[i + q * (m + 1)] * ks.y[q];
+        ks.y[i] = s / ks.H[i + i * (m + 1)];
+    }
+    for (int i = 0; i < k; ++i) set_coef(ks, i, sign * ks.y[i] * ks.vs[i]);
+}
+
 template <typename W>
-FDE_NI bool gmres_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol, const SolveParams& sp,
-                      SolveState& st, KShared& ks, unsigned char* work, int bytes) {
+FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol, const SolveParams& sp,
+                             SolveState& st, KShared& ks, const Wk& wk) {
     const long long N = I.N;
     const int m = I.restart;
-    const bool left = sp.side == FDE_SIDE_LEFT;
     GVecs<W> v = gmres_vecs<W>(I);
     long long lo, hi;
     team_range(t, N, lo, hi);
-
-    // ||rhs||
     {
         const W* a[1] = {rhs};
         if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
@@ -157,39 +316,22 @@ FDE_NI bool gmres_core(const Team& t, const Inst& I, int lm, const W* rhs, W* so
     const double nb = sqrt(ks.red[0]);
     if (!(nb > 0.0)) {  // zero right-hand side: x = 0 is exact
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sol[i] = W(0);
-        st.relres = 0.0;
-        st.relres_est = 0.0;
+        st.relres = st.relres_est = 0.0;
         st.status = FDE_OK;
         return team_sync(t);
     }
-    double ref = nb;       // left: ||P^-1 r_0||
-    bool first = true;
     st.status = FDE_ENOCONV;
     while (true) {
-        // r = rhs - A sol into V_0 (left: P^-1 of it)
-        if (!op_matvec<W>(t, I, lm, sol, W(1), v.w, v.tt, work, bytes)) return false;
-        W* rdst = left ? v.z : v.V;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) rdst[i] = ldw(rhs + i) - ldw(v.w + i);
-        if (!team_sync(t)) return false;
-        double beta, true_rel;
+        // V_0 = rhs - A sol (true residual)
+        if (!op_matvec_out<W>(t, I, lm, sol, W(1), v.tt, OutSpec<W>{kOutResid, v.V, rhs}, wk)) return false;
         {
-            const W* a[1] = {rdst};
-            if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
-            true_rel = sqrt(ks.red[0]) / nb;
-        }
-        if (left) {
-            if (!op_tau<W>(t, I, lm, v.z, W(1), v.V, work, bytes)) return false;
             const W* a[1] = {v.V};
             if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
-            beta = sqrt(ks.red[0]);
-            if (first) ref = beta;
-        } else {
-            beta = true_rel * nb;
         }
-        first = false;
-        st.relres = true_rel;
+        const double beta = sqrt(ks.red[0]);
+        st.relres = beta / nb;
         if (!finite(beta)) { st.status = FDE_ENONFINITE; break; }
-        if (beta <= sp.tol * ref || (left && beta == 0.0)) { st.status = FDE_OK; st.relres_est = beta / ref; break; }
+        if (beta <= sp.tol * nb) { st.status = FDE_OK; st.relres_est = beta / nb; break; }
         if (st.iterations >= sp.max_iters) { st.status = FDE_ENOCONV; break; }
         if (threadIdx.x == 0) {
             ks.vs[0] = 1.0 / beta;
@@ -198,109 +340,222 @@ FDE_NI bool gmres_core(const Team& t, const Inst& I, int lm, const W* rhs, W* so
         }
         __syncthreads();
         int k = 0;
-        bool cycle_converged = false;
+        int ncoef = 0;             // V_j = w - sum_{q < ncoef} coef_q V_q (j >= 1)
+        bool converged = false;
         for (int j = 0; j < m; ++j) {
-            const W sj = W(ks.vs[j]);
-            const W* vj = v.V + (long long)j * N;
-            if (left) {
-                if (!op_matvec<W>(t, I, lm, vj, sj, v.z, v.tt, work, bytes)) return false;
-                if (!op_tau<W>(t, I, lm, v.z, W(1), v.w, work, bytes)) return false;
+            Combo<W> u{};
+            u.V = v.V;
+            u.N = N;
+            u.s = W(ks.vs[j]);
+            if (j == 0) {
+                u.base = v.V;
             } else {
-                if (!op_tau<W>(t, I, lm, vj, sj, v.z, work, bytes)) return false;
-                if (!op_matvec<W>(t, I, lm, v.z, W(1), v.w, v.tt, work, bytes)) return false;
+                u.base = v.w;
+                u.c = kcoef<W>(ks);
+                u.cnt = ncoef;
+                u.store = v.V + (long long)j * N;
             }
+            if (!arnoldi_right<W>(t, I, lm, u, j + 1, v.V, v.z, v.w, v.tt, ks, wk)) return false;
             st.iterations++;
-            // pass 1: h = V^T w
-            if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, false, ks)) return false;
-            if (threadIdx.x <= j) ks.coef[threadIdx.x] = ks.red[threadIdx.x];
-            __syncthreads();
-            // w <- w - V h; pass 2: h2 = V^T w, ||w||^2
-            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                double acc = (double)ldw(v.w + i);
-                for (int q = 0; q <= j; ++q) acc -= ks.coef[q] * ks.vs[q] * (double)ldw(v.V + (long long)q * N + i);
-                v.w[i] = W(acc);
-            }
-            __syncthreads();
-            if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
-            double hn2 = ks.red[j + 1];
-            if (threadIdx.x == 0) {
+            trace_mark(t, 30);
+            const double ww = ks.red[j + 1];
+            double hh = 0.0;
+            for (int q = 0; q <= j; ++q) hh += ks.red[q] * ks.red[q];
+            double hn2;
+            if (hh < 0.5 * ww) {
+                // ||w - V h|| > ||w|| / sqrt(2) (the Daniel-Gragg-Kaufman-Stewart
+                // criterion): one classical Gram-Schmidt pass is enough,
+                // V_{j+1} = w - sum h_q vs_q V_q (formed by the next step)
+                hn2 = ww - hh;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int q = 0; q <= j; ++q) {
+                        ks.H[q + j * (m + 1)] = ks.red[q];
+                        set_coef(ks, q, ks.red[q] * ks.vs[q]);
+                    }
+                }
+            } else {
+                // reorthogonalise: w <- w - V h, then h2 = V^T w (V_j was stored
+                // by this step's first phase; the team barrier of the reduction
+                // made it visible)
+                __syncthreads();
+                if (threadIdx.x <= j) {
+                    set_coef(ks, threadIdx.x, ks.red[threadIdx.x] * ks.vs[threadIdx.x]);
+                    ks.y[threadIdx.x] = ks.red[threadIdx.x];
+                }
+                __syncthreads();
+                const W* kc = kcoef<W>(ks);
+                for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                    W acc = ldw(v.w + i);
+                    for (int q = 0; q <= j; ++q) acc -= kc[q] * ldw(v.V + (long long)q * N + i);
+                    v.w[i] = acc;
+                }
+                __syncthreads();
+                if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
+                trace_mark(t, 31);
                 double s2 = 0.0;
-                for (int q = 0; q <= j; ++q) {
-                    ks.H[q + j * (m + 1)] = ks.coef[q] + ks.red[q];
-                    s2 += ks.red[q] * ks.red[q];
+                for (int q = 0; q <= j; ++q) s2 += ks.red[q] * ks.red[q];
+                hn2 = ks.red[j + 1] - s2;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int q = 0; q <= j; ++q) {
+                        ks.H[q + j * (m + 1)] = ks.y[q] + ks.red[q];
+                        set_coef(ks, q, ks.red[q] * ks.vs[q]);
+                    }
                 }
-                ks.y[0] = hn2 - s2;       // ||w - V h2||^2
+            }
+            ncoef = j + 1;
+            const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
+            if (threadIdx.x == 0) {
+                ks.H[(j + 1) + j * (m + 1)] = hn;
+                givens_column(ks, j, m);
+                ks.vs[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
             }
             __syncthreads();
-            hn2 = ks.y[0];
-            const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
-            // V_{j+1} = w - V h2 (unnormalised), scale 1/hn
-            W* vn = v.V + (long long)(j + 1) * N;
-            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                double acc = (double)ldw(v.w + i);
-                for (int q = 0; q <= j; ++q) acc -= ks.red[q] * ks.vs[q] * (double)ldw(v.V + (long long)q * N + i);
-                vn[i] = W(acc);
-            }
-            double hnorm_ref = 0.0;
-            if (threadIdx.x == 0) {
-                double* Hc = ks.H + j * (m + 1);
-                Hc[j + 1] = hn;
-                for (int q = 0; q < j; ++q) {
-                    const double a = ks.cs[q] * Hc[q] + ks.sn[q] * Hc[q + 1];
-                    Hc[q + 1] = -ks.sn[q] * Hc[q] + ks.cs[q] * Hc[q + 1];
-                    Hc[q] = a;
-                }
-                const double den = hypot(Hc[j], Hc[j + 1]);
-                ks.cs[j] = den > 0.0 ? Hc[j] / den : 1.0;
-                ks.sn[j] = den > 0.0 ? Hc[j + 1] / den : 0.0;
-                Hc[j] = den;
-                Hc[j + 1] = 0.0;
-                ks.g[j + 1] = -ks.sn[j] * ks.g[j];
-                ks.g[j] = ks.cs[j] * ks.g[j];
-                ks.vs[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-                ks.y[1] = den;
-            }
-            if (!team_sync(t)) return false;
-            hnorm_ref = ks.y[1];
             const double est = fabs(ks.g[j + 1]);
+            const double diag = ks.H[j + j * (m + 1)];
             k = j + 1;
-            st.relres_est = est / ref;
+            st.relres_est = est / nb;
             if (!finite(est) || !finite(hn)) { st.status = FDE_ENONFINITE; break; }
-            const bool breakdown = !(hn > 1e-14 * hnorm_ref);
-            if (est <= sp.tol * ref || breakdown) { cycle_converged = true; break; }
+            const bool breakdown = !(hn > 1e-14 * diag);
+            if (est <= sp.tol * nb || breakdown) { converged = true; break; }
             if (st.iterations >= sp.max_iters) break;
         }
         if (st.status == FDE_ENONFINITE) break;
-        // y = H^{-1} g (k x k upper triangular), u = sum y_i vs_i V_i
-        if (threadIdx.x == 0) {
-            for (int i = k - 1; i >= 0; --i) {
-                double s = ks.g[i];
-                for (int q = i + 1; q < k; ++q) s -= ks.H[i + q * (m + 1)] * ks.y[q];
-                ks.y[i] = s / ks.H[i + i * (m + 1)];
-            }
-            for (int i = 0; i < k; ++i) ks.coef[i] = ks.y[i] * ks.vs[i];
-        }
+        // sol += P^{-1} (sum_i y_i vs_i V_i), the combination formed on the fly
+        if (threadIdx.x == 0) solve_triangle(ks, k, m, -1.0);
         __syncthreads();
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            double acc = 0.0;
-            for (int q = 0; q < k; ++q) acc += ks.coef[q] * (double)ldw(v.V + (long long)q * N + i);
-            v.tt[i] = W(acc);
-        }
-        if (!team_sync(t)) return false;
-        if (!left) {
-            if (!op_tau<W>(t, I, lm, v.tt, W(1), v.z, work, bytes)) return false;
-        }
-        const W* upd = left ? v.tt : v.z;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sol[i] = sol[i] + ldw(upd + i);
-        if (!team_sync(t)) return false;
-        // An inner solve trusts its estimate: below the working precision's
-        // floor a recomputed residual says nothing the outer FP64 residual won't.
-        if (sp.inner && (cycle_converged || st.iterations >= sp.max_iters)) {
-            st.status = cycle_converged ? FDE_OK : FDE_ENOCONV;
+        Combo<W> upd{};
+        upd.V = v.V;
+        upd.c = kcoef<W>(ks);
+        upd.cnt = k;
+        upd.N = N;
+        upd.s = W(1);
+        if (!op_tau_combo<W>(t, I, lm, upd, v.z, OutSpec<W>{kOutAdd, sol, nullptr}, wk)) return false;
+        if (sp.inner && (converged || st.iterations >= sp.max_iters)) {
+            // An inner solve trusts its estimate: below the working precision's
+            // floor a recomputed residual says nothing the outer FP64 residual won't.
+            st.status = converged ? FDE_OK : FDE_ENOCONV;
             break;
         }
         st.restarts++;
-        // loop: the true residual at the top decides
+    }
+    return team_sync(t);
+}
+
+template <typename W>
+FDE_NI bool gmres_left_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol, const SolveParams& sp,
+                            SolveState& st, KShared& ks, const Wk& wk) {
+    const long long N = I.N;
+    const int m = I.restart;
+    GVecs<W> v = gmres_vecs<W>(I);
+    long long lo, hi;
+    team_range(t, N, lo, hi);
+    {
+        const W* a[1] = {rhs};
+        if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
+    }
+    const double nb = sqrt(ks.red[0]);
+    if (!(nb > 0.0)) {
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sol[i] = W(0);
+        st.relres = st.relres_est = 0.0;
+        st.status = FDE_OK;
+        return team_sync(t);
+    }
+    double ref = nb;       // ||P^-1 r_0||
+    bool first = true;
+    st.status = FDE_ENOCONV;
+    while (true) {
+        if (!op_matvec_out<W>(t, I, lm, sol, W(1), v.tt, OutSpec<W>{kOutResid, v.z, rhs}, wk)) return false;
+        {
+            const W* a[1] = {v.z};
+            if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
+        }
+        st.relres = sqrt(ks.red[0]) / nb;
+        if (!op_tau<W>(t, I, lm, v.z, W(1), v.V, wk)) return false;
+        {
+            const W* a[1] = {v.V};
+            if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
+        }
+        const double beta = sqrt(ks.red[0]);
+        if (first) ref = beta;
+        first = false;
+        if (!finite(beta)) { st.status = FDE_ENONFINITE; break; }
+        if (beta <= sp.tol * ref || beta == 0.0) { st.status = FDE_OK; st.relres_est = beta / ref; break; }
+        if (st.iterations >= sp.max_iters) { st.status = FDE_ENOCONV; break; }
+        if (threadIdx.x == 0) {
+            ks.vs[0] = 1.0 / beta;
+            ks.g[0] = beta;
+            for (int i = 1; i <= m; ++i) ks.g[i] = 0.0;
+        }
+        __syncthreads();
+        int k = 0;
+        bool converged = false;
+        for (int j = 0; j < m; ++j) {
+            if (!op_matvec<W>(t, I, lm, v.V + (long long)j * N, W(ks.vs[j]), v.z, v.tt, wk)) return false;
+            if (!op_tau<W>(t, I, lm, v.z, W(1), v.w, wk)) return false;
+            st.iterations++;
+            if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, false, ks)) return false;
+            if (threadIdx.x <= j) {
+                ks.y[threadIdx.x] = ks.red[threadIdx.x];
+                set_coef(ks, threadIdx.x, ks.red[threadIdx.x] * ks.vs[threadIdx.x]);
+            }
+            __syncthreads();
+            const W* kc = kcoef<W>(ks);
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                W acc = ldw(v.w + i);
+                for (int q = 0; q <= j; ++q) acc -= kc[q] * ldw(v.V + (long long)q * N + i);
+                v.w[i] = acc;
+            }
+            __syncthreads();
+            if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
+            double s2 = 0.0;
+            for (int q = 0; q <= j; ++q) s2 += ks.red[q] * ks.red[q];
+            const double hn2 = ks.red[j + 1] - s2;
+            const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
+            __syncthreads();
+            if (threadIdx.x <= j) set_coef(ks, threadIdx.x, ks.red[threadIdx.x] * ks.vs[threadIdx.x]);
+            __syncthreads();
+            W* vn = v.V + (long long)(j + 1) * N;
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                W acc = ldw(v.w + i);
+                for (int q = 0; q <= j; ++q) acc -= kc[q] * ldw(v.V + (long long)q * N + i);
+                vn[i] = acc;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int q = 0; q <= j; ++q) ks.H[q + j * (m + 1)] = ks.y[q] + ks.red[q];
+                ks.H[(j + 1) + j * (m + 1)] = hn;
+                givens_column(ks, j, m);
+                ks.vs[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+            }
+            if (!team_sync(t)) return false;
+            const double est = fabs(ks.g[j + 1]);
+            const double diag = ks.H[j + j * (m + 1)];
+            k = j + 1;
+            st.relres_est = est / ref;
+            if (!finite(est) || !finite(hn)) { st.status = FDE_ENONFINITE; break; }
+            const bool breakdown = !(hn > 1e-14 * diag);
+            if (est <= sp.tol * ref || breakdown) { converged = true; break; }
+            if (st.iterations >= sp.max_iters) break;
+        }
+        if (st.status == FDE_ENONFINITE) break;
+        if (threadIdx.x == 0) solve_triangle(ks, k, m, 1.0);
+        __syncthreads();
+        {
+            const W* kc = kcoef<W>(ks);
+            for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                W acc = sol[i];
+                for (int q = 0; q < k; ++q) acc += kc[q] * ldw(v.V + (long long)q * N + i);
+                sol[i] = acc;
+            }
+        }
+        if (!team_sync(t)) return false;
+        if (sp.inner && (converged || st.iterations >= sp.max_iters)) {
+            st.status = converged ? FDE_OK : FDE_ENOCONV;
+            break;
+        }
+        st.restarts++;
     }
     return team_sync(t);
 }
@@ -311,7 +566,7 @@ FDE_NI bool gmres_core(const Team& t, const Inst& I, int lm, const W* rhs, W* so
 
 template <typename W>
 FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol, const SolveParams& sp,
-                    SolveState& st, KShared& ks, unsigned char* work, int bytes) {
+                     SolveState& st, KShared& ks, const Wk& wk) {
     const long long N = I.N;
     W* base = reinterpret_cast<W*>(I.wvec);
     W* r = base;
@@ -332,9 +587,7 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
         st.status = FDE_OK;
         return team_sync(t);
     }
-    if (!op_matvec<W>(t, I, lm, sol, W(1), q, tt, work, bytes)) return false;
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) r[i] = ldw(rhs + i) - ldw(q + i);
-    if (!team_sync(t)) return false;
+    if (!op_matvec_out<W>(t, I, lm, sol, W(1), tt, OutSpec<W>{kOutResid, r, rhs}, wk)) return false;
     {
         const W* a[1] = {r};
         if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
@@ -343,7 +596,7 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
     st.relres = st.relres_est = sqrt(rr) / nb;
     st.status = FDE_ENOCONV;
     if (sqrt(rr) <= sp.tol * nb) { st.status = FDE_OK; return team_sync(t); }
-    if (!op_tau<W>(t, I, lm, r, W(1), z, work, bytes)) return false;
+    if (!op_tau<W>(t, I, lm, r, W(1), z, wk)) return false;
     {
         const W* a[1] = {r};
         const W* b[1] = {z};
@@ -353,7 +606,7 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
     for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) p[i] = ldw(z + i);
     if (!team_sync(t)) return false;
     while (st.iterations < sp.max_iters) {
-        if (!op_matvec<W>(t, I, lm, p, W(1), q, tt, work, bytes)) return false;
+        if (!op_matvec<W>(t, I, lm, p, W(1), q, tt, wk)) return false;
         st.iterations++;
         {
             const W* a[1] = {p};
@@ -364,11 +617,12 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
         if (!finite(pq)) { st.status = FDE_ENONFINITE; break; }
         if (!(pq > 0.0)) { st.status = FDE_EBREAKDOWN; break; }
         const double al = rz / pq;
+        const W alw = W(al);
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            sol[i] = W((double)sol[i] + al * (double)ldw(p + i));
-            r[i] = W((double)ldw(r + i) - al * (double)ldw(q + i));
+            sol[i] = sol[i] + alw * ldw(p + i);
+            r[i] = ldw(r + i) - alw * ldw(q + i);
         }
-        if (!team_sync(t)) return false;
+        __syncthreads();
         {
             const W* a[1] = {r};
             if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
@@ -377,7 +631,7 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
         st.relres_est = sqrt(rr) / nb;
         if (!finite(rr)) { st.status = FDE_ENONFINITE; break; }
         if (sqrt(rr) <= sp.tol * nb) { st.status = FDE_OK; break; }
-        if (!op_tau<W>(t, I, lm, r, W(1), z, work, bytes)) return false;
+        if (!op_tau<W>(t, I, lm, r, W(1), z, wk)) return false;
         {
             const W* a[1] = {r};
             const W* b[1] = {z};
@@ -386,7 +640,8 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
         const double rz_new = ks.red[0];
         const double be = rz_new / rz;
         rz = rz_new;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) p[i] = W((double)ldw(z + i) + be * (double)ldw(p + i));
+        const W bew = W(be);
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) p[i] = ldw(z + i) + bew * ldw(p + i);
         if (!team_sync(t)) return false;
     }
     if (sp.inner) {
@@ -394,9 +649,7 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
         return team_sync(t);
     }
     // true residual of the final iterate
-    if (!op_matvec<W>(t, I, lm, sol, W(1), q, tt, work, bytes)) return false;
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) r[i] = ldw(rhs + i) - ldw(q + i);
-    if (!team_sync(t)) return false;
+    if (!op_matvec_out<W>(t, I, lm, sol, W(1), tt, OutSpec<W>{kOutResid, r, rhs}, wk)) return false;
     {
         const W* a[1] = {r};
         if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
@@ -407,9 +660,10 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
 
 template <typename W>
 FDE_D bool krylov_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol, const SolveParams& sp,
-                       SolveState& st, KShared& ks, unsigned char* work, int bytes) {
-    if (I.method == FDE_PCG) return pcg_core<W>(t, I, lm, rhs, sol, sp, st, ks, work, bytes);
-    return gmres_core<W>(t, I, lm, rhs, sol, sp, st, ks, work, bytes);
+                       SolveState& st, KShared& ks, const Wk& wk) {
+    if (I.method == FDE_PCG) return pcg_core<W>(t, I, lm, rhs, sol, sp, st, ks, wk);
+    if (sp.side == FDE_SIDE_LEFT) return gmres_left_core<W>(t, I, lm, rhs, sol, sp, st, ks, wk);
+    return gmres_right_core<W>(t, I, lm, rhs, sol, sp, st, ks, wk);
 }
 
 }  // namespace fde

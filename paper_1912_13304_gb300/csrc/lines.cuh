@@ -19,6 +19,10 @@
 //   tau^{-1} : mu = 1/(L F(theta_k)) on the odd extension, which equals
 //              S diag(1/F) S (the two sine transforms of Sec. 1)
 //   S r      : the odd-extension spectrum itself, S r = sqrt(2/Np) (-Im X_j / 2)
+//
+// Shared-memory line buffers hold lines at stride Np in a flat index space
+// and are accessed through pad(); a second output set (kMulLam2) occupies
+// the lines that follow the first set.
 #pragma once
 
 #include "fft.cuh"
@@ -41,31 +45,19 @@ FDE_D cx<float> ldw(const cx<float>* p) {
     return mk(v.x, v.y);
 }
 
-// Real input line: r_k = scale * base[(k-1) stride] (* pre[(k-1) stride]).
-template <typename W>
-struct RealIn {
-    const W* base;
-    long long stride;
-    W scale;
-    const W* pre;
-    FDE_D W get(int k) const {
-        const long long o = (long long)(k - 1) * stride;
-        W v = ldw(base + o) * scale;
-        if (pre) v *= __ldg(pre + o);
-        return v;
-    }
-};
-
-template <typename W, int EXT>
-FDE_D W ext_val(const RealIn<W>& in, int k, int n, int Np) {
-    if (k >= 1 && k <= n) return in.get(k);
-    if (EXT == kExtOdd && k > Np) return -in.get(2 * Np - k);
+// v_k of the length-L extension of a line.  get(k, direct) returns r_k
+// (1 <= k <= n); `direct` is true for exactly one read of every r_k (the
+// unmirrored one), so a getter may store or accumulate there.
+template <typename W, int EXT, typename GetF>
+FDE_D W ext_val(GetF& get, int k, int n, int Np) {
+    if (k >= 1 && k <= n) return get(k, true);
+    if (EXT == kExtOdd && k > Np) return -get(2 * Np - k, false);
     return W(0);
 }
 
-template <typename W, int EXT>
-FDE_D cx<W> pack_elem(const RealIn<W>& in, int m, int n, int Np) {
-    return mk(ext_val<W, EXT>(in, 2 * m, n, Np), ext_val<W, EXT>(in, 2 * m + 1, n, Np));
+template <typename W, int EXT, typename GetF>
+FDE_D cx<W> pack_elem(GetF& get, int m, int n, int Np) {
+    return mk(ext_val<W, EXT>(get, 2 * m, n, Np), ext_val<W, EXT>(get, 2 * m + 1, n, Np));
 }
 
 template <typename R>
@@ -126,50 +118,51 @@ struct Mult {
 };
 
 // ---------------------------------------------------------------------------
-// Whole lines held by one CTA (shared memory).  B lines of Np complex values
-// at stride Np; `buf2` holds the second output of kMulLam2.
+// Whole lines held by one CTA: B lines of Np complex values, flat index
+// l * Np + m through pad().
 // ---------------------------------------------------------------------------
 
-// Pack B real lines into buf.  in[l] describes line l.  COLMAJOR maps
-// consecutive threads to consecutive lines (coalesced for strided columns).
-template <typename W, int EXT, bool COLMAJOR, typename InF>
-FDE_D void cta_pack(cx<W>* buf, int B, int n, int Np, InF in_of_line) {
+// Pack B real lines.  get(l, k, direct) returns r_k of line l.  COLMAJOR
+// maps consecutive threads to consecutive lines (coalesced for strided
+// columns).
+template <typename W, int EXT, bool COLMAJOR, typename GetF>
+FDE_D void cta_pack(cx<W>* buf, int B, int n, int Np, GetF get) {
     const int total = B * Np;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int l, m;
         if (COLMAJOR) { l = idx % B; m = idx / B; }
         else { m = idx % Np; l = idx / Np; }
-        buf[l * Np + m] = pack_elem<W, EXT>(in_of_line(l), m, n, Np);
+        auto g = [&](int k, bool direct) { return get(l, k, direct); };
+        buf[pad(l * Np + m)] = pack_elem<W, EXT>(g, m, n, Np);
     }
     __syncthreads();
 }
 
-// Spectral step on all pairs of B lines.  col_of_line gives kMulTau2's
-// x-frequency index of a line.
+// Spectral step on all pairs of B lines; the second output (kMulLam2) goes
+// to lines B..2B-1.  col_of_line gives kMulTau2's x-frequency of a line.
 template <typename W, typename ColF>
-FDE_D void cta_spectral(cx<W>* buf, cx<W>* buf2, int B, int Np, int logNp, const cx<W>* tw, int logTW,
-                        const Mult<W>& mu, ColF col_of_line) {
+FDE_D void cta_spectral(cx<W>* buf, int B, int Np, int logNp, const Tw& tw, const Mult<W>& mu,
+                        ColF col_of_line) {
     const int half = Np / 2 + 1;
-    const int wsh = logTW - (logNp + 1);
     const bool two = mu.kind == kMulLam2;
     for (int idx = threadIdx.x; idx < B * half; idx += blockDim.x) {
         const int l = idx / half;
         const int j = idx - l * half;
         const int jm = (Np - j) & (Np - 1);
-        cx<W>* z = buf + l * Np;
-        const cx<W> wj = tw[j << wsh];
+        const int o = l * Np;
+        const cx<W> wj = tw_L<W>(tw, j, logNp + 1);
         cx<W> a, b, al, be, al2, be2;
-        unpack_pair(z[j], z[jm], wj, a, b);
+        unpack_pair(buf[pad(o + j)], buf[pad(o + jm)], wj, a, b);
         mu.apply(j, col_of_line(l), a, b, al, be, al2, be2);
         cx<W> Qj, Qm;
         repack_pair(al, be, wj, Qj, Qm);
-        z[j] = Qj;
-        if (jm != j) z[jm] = Qm;
+        buf[pad(o + j)] = Qj;
+        if (jm != j) buf[pad(o + jm)] = Qm;
         if (two) {
-            cx<W>* z2 = buf2 + l * Np;
+            const int o2 = (B + l) * Np;
             repack_pair(al2, be2, wj, Qj, Qm);
-            z2[j] = Qj;
-            if (jm != j) z2[jm] = Qm;
+            buf[pad(o2 + j)] = Qj;
+            if (jm != j) buf[pad(o2 + jm)] = Qm;
         }
     }
     __syncthreads();
@@ -177,41 +170,40 @@ FDE_D void cta_spectral(cx<W>* buf, cx<W>* buf2, int B, int Np, int logNp, const
 
 // Lone DST-I of B lines: after the forward FFT of the odd extension, write
 // the unnormalised sine sums s_j = -Im X_j / 2 (j = 1..n) into the real
-// shared-memory array s (B lines at stride Np).
+// shared-memory array s (B lines at stride Np, unpadded).
 template <typename W>
-FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, const cx<W>* tw, int logTW) {
+FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, const Tw& tw) {
     const int half = Np / 2 + 1;
-    const int wsh = logTW - (logNp + 1);
     for (int idx = threadIdx.x; idx < B * half; idx += blockDim.x) {
         const int l = idx / half;
         const int j = idx - l * half;
         const int jm = (Np - j) & (Np - 1);
-        const cx<W>* z = buf + l * Np;
+        const int o = l * Np;
         cx<W> a, b;
-        unpack_pair(z[j], z[jm], tw[j << wsh], a, b);
+        unpack_pair(buf[pad(o + j)], buf[pad(o + jm)], tw_L<W>(tw, j, logNp + 1), a, b);
         if (j >= 1) {
-            s[l * Np + j] = W(-0.5) * a.y;
-            if (jm != j) s[l * Np + (Np - j)] = W(0.5) * b.y;
+            s[o + j] = W(-0.5) * a.y;
+            if (jm != j) s[o + (Np - j)] = W(0.5) * b.y;
         }
     }
     __syncthreads();
 }
 
-// Unpack q_m = a_{2m} + i a_{2m+1} and hand a_k (k = 1..n) to epi(l, k-1, a_k [, b_k]).
+// Unpack q_m = a_{2m} + i a_{2m+1} and hand a_k (k = 1..n) to
+// epi(l, k-1, a_k, b_k), b from the second output set when TWO.
 template <typename W, bool COLMAJOR, bool TWO, typename EpiF>
-FDE_D void cta_unpack(const cx<W>* buf, const cx<W>* buf2, int B, int n, int Np, EpiF epi) {
-    // element k of line l lives in buf[l*Np + k/2] (.x if k even, .y if odd)
+FDE_D void cta_unpack(const cx<W>* buf, int B, int n, int Np, EpiF epi) {
     const int total = B * n;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int l, p;
         if (COLMAJOR) { l = idx % B; p = idx / B; }
         else { p = idx % n; l = idx / n; }
         const int k = p + 1;
-        const cx<W> q = buf[l * Np + (k >> 1)];
+        const cx<W> q = buf[pad(l * Np + (k >> 1))];
         const W va = (k & 1) ? q.y : q.x;
         W vb = W(0);
         if (TWO) {
-            const cx<W> q2 = buf2[l * Np + (k >> 1)];
+            const cx<W> q2 = buf[pad((B + l) * Np + (k >> 1))];
             vb = (k & 1) ? q2.y : q2.x;
         }
         epi(l, p, va, vb);

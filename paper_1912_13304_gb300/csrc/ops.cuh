@@ -1,34 +1,40 @@
 // The two operators of one Krylov iteration, for every data layout:
 //   op_matvec: y = M (s x)      (Sec. 1.2 / 1.4, Toeplitz by circulant embedding)
 //   op_tau:    z = P^{-1} (s r) (Sec. 3.1 / 3.2, DST-I / symbol / DST-I)
+// and the phases that the fused right-preconditioned Arnoldi step combines.
+//
 // Layouts: a 1D line held whole by one CTA; a 1D line split across the CTAs
-// of a team (Np = P1 * P2, column / row / column phases through an L2-resident
-// intermediate); a 2D plane (row lines along x, column lines along y).
-// Every operator ends with a team barrier, so its output is complete on return.
+// of a team (Np = P1 * P2: column / row / column phases through an
+// L2-resident intermediate Y); a 2D plane (row lines along x, column lines
+// along y).  Phase functions take a getter for their input (so a basis
+// vector can be formed on the fly) and an epilogue for their output.
 #pragma once
 
 #include "lines.cuh"
 
 namespace fde {
 
-template <typename W> struct Ept { static constexpr int v = sizeof(W) == 4 ? 32 : 16; };
-
 template <typename W>
 FDE_D W coef(const W* arr, double cst, long long i) {
     return arr ? __ldg(arr + i) : W(cst);
 }
 
-// Lines of Np complex values that fit the register staging of fft_inplace and
-// `bytes` of shared memory, with `nbuf` buffers per line.
+// Shared memory and twiddles of one CTA for transform phases.
+struct Wk {
+    unsigned char* smem;
+    int bytes;
+    Tw tw;
+};
+
+// Lines of Np complex values (nbuf buffers each, padded) plus `extra_real`
+// real arrays of Np per line that fit `bytes` of shared memory.
 template <typename W>
-FDE_HD int max_lines(int Np, int nbuf, int bytes) {
-    const int by_regs = (Ept<W>::v * kThreads) / (Np * nbuf);
-    const int by_smem = bytes / (int)(Np * nbuf * sizeof(cx<W>));
-    int b = by_regs < by_smem ? by_regs : by_smem;
-    return b;
+FDE_HD int max_lines(int Np, int nbuf, int bytes, int extra_real = 0) {
+    const long long per = (long long)Np * nbuf * sizeof(cx<W>) * 17 / 16 + (long long)Np * extra_real * sizeof(W) + 16;
+    return (int)((bytes - 64) / per);
 }
 
-FDE_D int pow2_floor(int v) { int p = 1; while (p * 2 <= v) p *= 2; return p; }
+FDE_HD int pow2_floor(int v) { int p = 1; while (p * 2 <= v) p *= 2; return p; }
 
 // ---------------------------------------------------------------------------
 // Multipliers
@@ -67,239 +73,386 @@ FDE_D Mult<W> mult_tau2(const Inst& I) {
 }
 
 // ---------------------------------------------------------------------------
-// 1D, whole line in one CTA
+// Inputs formed on the fly: u_p = s * (base_p - sum_q c_q V_q[p]) where V_q
+// are basis vectors at stride N.  `store` (optional) receives the
+// unscaled value base_p - sum ... on the element's direct read.
 // ---------------------------------------------------------------------------
 
 template <typename W>
-FDE_NI void cta_matvec_1d(const Inst& I, const W* x, W s, W* y, unsigned char* work) {
+struct Combo {
+    const W* base;         // may be null (then 0)
+    const W* V;
+    const W* c;            // shared memory, cnt coefficients (working precision)
+    int cnt;
+    long long N;
+    W s;
+    W* store;
+    const W* pre;          // optional elementwise prescale applied after s (D^{-1} for P = D tau)
+
+    // In the working precision: a basis update is a vector operation, not an
+    // inner product.
+    FDE_D W raw(long long p) const {
+        W v = base ? ldw(base + p) : W(0);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) v -= c[q] * ldw(V + (long long)q * N + p);
+        return v;
+    }
+    FDE_D W get(long long p, bool direct) const {
+        const W r = raw(p);
+        if (direct && store) store[p] = r;
+        W v = s * r;
+        if (pre) v *= __ldg(pre + p);
+        return v;
+    }
+};
+
+template <typename W>
+FDE_D Combo<W> combo_vec(const W* x, W s, const W* pre = nullptr) {
+    Combo<W> c{};
+    c.base = x;
+    c.s = s;
+    c.pre = pre;
+    return c;
+}
+
+
+// ---------------------------------------------------------------------------
+// Epilogues.  A transform hands (a, b) per element (b: the second product of
+// a two-multiplier matvec); the epilogue forms the value and writes it.
+// ---------------------------------------------------------------------------
+
+enum ValKind : int { kValA = 0, kValMvX = 1, kValMvY = 2 };
+enum OutKind : int { kOutStore = 0, kOutResid = 1, kOutAdd = 2 };
+
+// Where a result goes: out = v, out = rhs - v, or out += v.
+template <typename W>
+struct OutSpec {
+    int outk;
+    W* out;
+    const W* rhs;
+};
+
+template <typename W>
+FDE_D OutSpec<W> out_store(W* out) { return OutSpec<W>{kOutStore, out, nullptr}; }
+
+template <typename W>
+struct Epi {
+    int val;               // kValA: a (* post); kValMvX: c0 s x + c+ a + c- b; kValMvY: tmp + sr (c+ a + c- b)
+    OutSpec<W> o;
+    const W* post;
+    const W* x;
+    W xs, c0, sr;
+    const W* cp;
+    const W* cm;
+    double cpc, cmc;
+    int sym;
+    const W* tmp;
+
+    FDE_D W value(long long p, W a, W b) const {
+        if (val == kValA) return post ? a * __ldg(post + p) : a;
+        W v = (cp ? __ldg(cp + p) : W(cpc)) * a;
+        if (!sym) v += (cm ? __ldg(cm + p) : W(cmc)) * b;
+        if (val == kValMvX) return c0 * xs * ldw(x + p) + v;
+        return ldw(tmp + p) + sr * v;
+    }
+    FDE_D void operator()(long long p, W a, W b) const {
+        const W v = value(p, a, b);
+        if (o.outk == kOutStore) o.out[p] = v;
+        else if (o.outk == kOutResid) o.out[p] = ldw(o.rhs + p) - v;
+        else o.out[p] = o.out[p] + v;
+    }
+};
+
+template <typename W>
+FDE_D Epi<W> epi_a(const W* post, OutSpec<W> o) {
+    Epi<W> e{};
+    e.val = kValA;
+    e.post = post;
+    e.o = o;
+    return e;
+}
+
+// x part (1D: the whole matvec): c0 s x + D_+ a + D_- b.
+template <typename W>
+FDE_D Epi<W> epi_mvx(const Inst& I, const W* x, W s, OutSpec<W> o) {
+    Epi<W> e{};
+    e.val = kValMvX;
+    e.o = o;
+    e.x = x;
+    e.xs = s;
+    e.c0 = W(I.c0);
+    e.cp = Prec<W>::dp(I);
+    e.cm = Prec<W>::dm(I);
+    e.cpc = I.dpc;
+    e.cmc = I.dmc;
+    e.sym = I.symx;
+    return e;
+}
+
+// y part (2D): tmp + sr (E_+ a + E_- b).
+template <typename W>
+FDE_D Epi<W> epi_mvy(const Inst& I, const W* tmp, OutSpec<W> o) {
+    Epi<W> e{};
+    e.val = kValMvY;
+    e.o = o;
+    e.tmp = tmp;
+    e.sr = W(I.sr);
+    e.cp = Prec<W>::ep(I);
+    e.cm = Prec<W>::em(I);
+    e.cpc = I.epc;
+    e.cmc = I.emc;
+    e.sym = I.symy;
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// 1D, whole line in one CTA (team of one)
+// ---------------------------------------------------------------------------
+
+// z = tau^{-1}(u); epi(p, z_p).  D^{-1} per the order is applied here.
+template <typename W>
+FDE_NI void cta_tau_1d(const Inst& I, const Wk& wk, Combo<W> u, Epi<W> epi) {
     const AxisData& A = I.ax[0];
     const int n = A.n, Np = A.Np;
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
-    cx<W>* buf2 = buf + Np;
-    const bool sym = I.symx;
-    const RealIn<W> in{x, 1, s, nullptr};
-    cta_pack<W, kExtZero, false>(buf, 1, n, Np, [&](int) { return in; });
-    fft_inplace<W, Ept<W>::v, false>(buf, A.logNp, 1, Np, Prec<W>::tw(I), I.logTW);
-    const Mult<W> mu = mult_matvec<W>(A, sym);
-    cta_spectral<W>(buf, buf2, 1, Np, A.logNp, Prec<W>::tw(I), I.logTW, mu, [](int) { return 0; });
-    fft_inplace<W, Ept<W>::v, true>(buf, A.logNp, sym ? 1 : 2, Np, Prec<W>::tw(I), I.logTW);
-    const W c0s = W(I.c0) * s;
-    const W* dp = Prec<W>::dp(I);
-    const W* dm = Prec<W>::dm(I);
-    if (sym) {
-        cta_unpack<W, false, false>(buf, buf2, 1, n, Np, [&](int, int p, W va, W) {
-            y[p] = c0s * ldw(x + p) + coef(dp, I.dpc, p) * va;
-        });
-    } else {
-        cta_unpack<W, false, true>(buf, buf2, 1, n, Np, [&](int, int p, W va, W vb) {
-            y[p] = c0s * ldw(x + p) + coef(dp, I.dpc, p) * va + coef(dm, I.dmc, p) * vb;
-        });
-    }
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    const W* dinv = Prec<W>::dinv(I);
+    if (I.has_D && I.order == FDE_ORDER_D_TAU) u.pre = dinv;
+    if (I.has_D && I.order == FDE_ORDER_TAU_D) epi.post = dinv;
+    cta_pack<W, kExtOdd, false>(buf, 1, n, Np, [&](int, int k, bool d) { return u.get(k - 1, d); });
+    fft_lines<W, false>(buf, A.logNp, 1, Np, wk.tw);
+    cta_spectral<W>(buf, 1, Np, A.logNp, wk.tw, mult_tau1<W>(A), [](int) { return 0; });
+    fft_lines<W, true>(buf, A.logNp, 1, Np, wk.tw);
+    cta_unpack<W, false, false>(buf, 1, n, Np, [&](int, int p, W va, W vb) { epi(p, va, vb); });
     __syncthreads();
 }
 
+// the matvec of s x; epi(p, (T x)_p, (T^T x)_p) -- symmetric: ((T+T^T) x)_p.
 template <typename W>
-FDE_NI void cta_tau_1d(const Inst& I, const W* r, W s, W* z, unsigned char* work) {
+FDE_NI void cta_matvec_1d(const Inst& I, const Wk& wk, const W* x, W s, Epi<W> epi) {
     const AxisData& A = I.ax[0];
     const int n = A.n, Np = A.Np;
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
-    const W* dinv = Prec<W>::dinv(I);
-    const bool pre = I.has_D && I.order == FDE_ORDER_D_TAU;
-    const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;
-    const RealIn<W> in{r, 1, s, pre ? dinv : nullptr};
-    cta_pack<W, kExtOdd, false>(buf, 1, n, Np, [&](int) { return in; });
-    fft_inplace<W, Ept<W>::v, false>(buf, A.logNp, 1, Np, Prec<W>::tw(I), I.logTW);
-    const Mult<W> mu = mult_tau1<W>(A);
-    cta_spectral<W>(buf, nullptr, 1, Np, A.logNp, Prec<W>::tw(I), I.logTW, mu, [](int) { return 0; });
-    fft_inplace<W, Ept<W>::v, true>(buf, A.logNp, 1, Np, Prec<W>::tw(I), I.logTW);
-    cta_unpack<W, false, false>(buf, nullptr, 1, n, Np, [&](int, int p, W va, W) {
-        z[p] = post ? va * __ldg(dinv + p) : va;
-    });
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    const bool sym = I.symx;
+    cta_pack<W, kExtZero, false>(buf, 1, n, Np, [&](int, int k, bool) { return s * ldw(x + (k - 1)); });
+    fft_lines<W, false>(buf, A.logNp, 1, Np, wk.tw);
+    cta_spectral<W>(buf, 1, Np, A.logNp, wk.tw, mult_matvec<W>(A, sym), [](int) { return 0; });
+    fft_lines<W, true>(buf, A.logNp, sym ? 1 : 2, Np, wk.tw);
+    if (sym) cta_unpack<W, false, false>(buf, 1, n, Np, [&](int, int p, W va, W vb) { epi(p, va, vb); });
+    else cta_unpack<W, false, true>(buf, 1, n, Np, [&](int, int p, W va, W vb) { epi(p, va, vb); });
     __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
 // 1D, line split across a team: Np = P1 * P2, m = P2 m1 + m2, j = j1 + P1 j2.
+// Column units hold cc consecutive columns m2; row units hold rows
+// {j1, P1 - j1} whose spectral pairs (j, Np - j) meet in one unit.
 // ---------------------------------------------------------------------------
 
 template <typename W>
-FDE_D int split_cols_per_unit(const AxisData& A, int team_size, int nbuf, int bytes) {
-    int cap = max_lines<W>(A.P1, nbuf, bytes);
-    int want = A.P2 / team_size;
+FDE_D int split_cols_per_unit(const AxisData& A, int team_size, int bytes) {
+    const int cap_smem = max_lines<W>(A.P1, 2, bytes);
+    const int cap_fft = fft_lines_per_call(A.logP1, kThreads);
+    const int cap = cap_smem < cap_fft ? cap_smem : cap_fft;
     int cc = 1;
-    while (cc < want) cc *= 2;          // units <= team size when possible
+    while (cc * team_size < A.P2) cc *= 2;          // units <= team size when possible
     if (cc > cap) cc = pow2_floor(cap);
     if (cc > A.P2) cc = A.P2;
-    if (cc < 1) cc = 1;
-    return cc;
+    return cc < 1 ? 1 : cc;
 }
 
-// Column phase of the forward transform: pack, P1-point FFTs, twiddle,
-// store Y[j1][m2].
+// Element positions p (0-based) whose outputs a column unit [m2b, m2b+cc)
+// produces: k = 2m, 2m+1 (1 <= k <= n), m = P2 m1 + m2, m1 < P1/2.
+template <typename F>
+FDE_D void split_unit_elements(const AxisData& A, int m2b, int cc, F f) {
+    const int total = (A.P1 / 2) * cc * 2;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int m1 = idx / (2 * cc);
+        const int rem = idx - m1 * 2 * cc;
+        const long long k = 2LL * (A.P2 * m1 + m2b + (rem >> 1)) + (rem & 1);
+        if (k >= 1 && k <= A.n) f(k - 1);
+    }
+}
+
+// Forward column phase: pack the extension of u, P1-point FFTs, twiddle,
+// Y[j1][m2].
 template <typename W, int EXT>
-FDE_NI void split_fwd_cols(const Team& t, const Inst& I, const RealIn<W>& in, cx<W>* Y, unsigned char* work,
-                          int cc) {
+FDE_NI void split_fwd_cols(const Team& t, const Inst& I, const Wk& wk, Combo<W> u, cx<W>* Y, int cc) {
     const AxisData& A = I.ax[0];
     const int n = A.n, Np = A.Np, P1 = A.P1, P2 = A.P2;
-    const cx<W>* tw = Prec<W>::tw(I);
-    const int tsh = I.logTW - A.logNp;
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    const int tsh = wk.tw.logTW - A.logNp;
+    const cx<W>* g = tw_global_table<W>(wk.tw);
+    auto get = [&](int k, bool d) { return u.get(k - 1, d); };
     const int units = P2 / cc;
-    for (int u = t.rank; u < units; u += t.size) {
-        const int m2b = u * cc;
+    for (int un = t.rank; un < units; un += t.size) {
+        const int m2b = un * cc;
         for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
             const int c = idx % cc, m1 = idx / cc;
-            buf[c * P1 + m1] = pack_elem<W, EXT>(in, P2 * m1 + m2b + c, n, Np);
+            buf[pad(c * P1 + m1)] = pack_elem<W, EXT>(get, P2 * m1 + m2b + c, n, Np);
         }
         __syncthreads();
-        fft_inplace<W, Ept<W>::v, false>(buf, A.logP1, cc, P1, tw, I.logTW);
+        fft_lines<W, false>(buf, A.logP1, cc, P1, wk.tw);
         for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
             const int c = idx % cc, j1 = idx / cc;
             const int m2 = m2b + c;
-            Y[(long long)j1 * P2 + m2] = buf[c * P1 + j1] * tw[(j1 * m2) << tsh];
+            Y[(long long)j1 * P2 + m2] = buf[pad(c * P1 + j1)] * g[(j1 * m2) << tsh];
         }
         __syncthreads();
     }
 }
 
-// Row phase: P2-point FFTs of rows {j1, P1-j1}, the spectral step on the
-// pairs (j, Np-j), inverse P2-point FFTs, inverse twiddle; results back to Y
-// (and Y2 for the second multiplier).
+// Row phase: P2-point FFTs of rows {j1, P1-j1}, spectral step on the pairs
+// (j, Np-j), inverse FFTs, inverse twiddle; back to Y (and Y2).
 template <typename W>
-FDE_NI void split_rows(const Team& t, const Inst& I, const Mult<W>& mu, cx<W>* Y, cx<W>* Y2,
-                      unsigned char* work) {
+FDE_NI void split_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W> mu, cx<W>* Y, cx<W>* Y2) {
+    trace_mark(t, 40);
     const AxisData& A = I.ax[0];
     const int P1 = A.P1, P2 = A.P2;
-    const cx<W>* tw = Prec<W>::tw(I);
-    const int wsh = I.logTW - (A.logNp + 1);
-    const int tsh = I.logTW - A.logNp;
+    const int tsh = wk.tw.logTW - A.logNp;
+    const cx<W>* g = tw_global_table<W>(wk.tw);
     const bool two = mu.kind == kMulLam2;
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const int units = P1 / 2 + 1;
     for (int u = t.rank; u < units; u += t.size) {
         const int nrows = u < 2 ? 1 : 2;
         int rows[2];
         rows[0] = u == 0 ? 0 : (u == 1 ? P1 / 2 : u - 1);
         rows[1] = P1 - rows[0];
-        cx<W>* buf2 = buf + nrows * P2;
         for (int idx = threadIdx.x; idx < nrows * P2; idx += blockDim.x) {
             const int sl = idx / P2, j2 = idx - sl * P2;
-            buf[idx] = ldw(Y + (long long)rows[sl] * P2 + j2);
+            buf[pad(idx)] = ldw(Y + (long long)rows[sl] * P2 + j2);
         }
         __syncthreads();
-        fft_inplace<W, Ept<W>::v, false>(buf, A.logP2, nrows, P2, tw, I.logTW);
+        trace_mark(t, 41);
+        fft_lines<W, false>(buf, A.logP2, nrows, P2, wk.tw);
+        trace_mark(t, 42);
         const int npairs = u == 0 ? P2 / 2 + 1 : (u == 1 ? P2 / 2 : P2);
+        const int o2 = nrows * P2;            // second output set
         for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
-            int sj, j2, sm, j2m;
-            if (u == 0) { sj = 0; j2 = q; sm = 0; j2m = (P2 - q) & (P2 - 1); }
-            else if (u == 1) { sj = 0; j2 = q; sm = 0; j2m = P2 - 1 - q; }
-            else { sj = 0; j2 = q; sm = 1; j2m = P2 - 1 - q; }
-            const int j = rows[sj] + P1 * j2;              // frequency of the first element
-            const cx<W> wj = tw[j << wsh];
+            const int j2 = q;
+            const int sm = u >= 2 ? 1 : 0;
+            const int j2m = u == 0 ? ((P2 - q) & (P2 - 1)) : P2 - 1 - q;
+            const int j = rows[0] + P1 * j2;           // frequency of the first element
+            const cx<W> wj = tw_L<W>(wk.tw, j, A.logNp + 1);
+            const int ia = j2, ib = sm * P2 + j2m;
             cx<W> a, b, al, be, al2, be2;
-            unpack_pair(buf[sj * P2 + j2], buf[sm * P2 + j2m], wj, a, b);
+            unpack_pair(buf[pad(ia)], buf[pad(ib)], wj, a, b);
             mu.apply(j, 0, a, b, al, be, al2, be2);
             cx<W> Qj, Qm;
             repack_pair(al, be, wj, Qj, Qm);
-            const bool self = (sm == sj) && (j2m == j2);
-            buf[sj * P2 + j2] = Qj;
-            if (!self) buf[sm * P2 + j2m] = Qm;
+            buf[pad(ia)] = Qj;
+            if (ib != ia) buf[pad(ib)] = Qm;
             if (two) {
                 repack_pair(al2, be2, wj, Qj, Qm);
-                buf2[sj * P2 + j2] = Qj;
-                if (!self) buf2[sm * P2 + j2m] = Qm;
+                buf[pad(o2 + ia)] = Qj;
+                if (ib != ia) buf[pad(o2 + ib)] = Qm;
             }
         }
         __syncthreads();
-        fft_inplace<W, Ept<W>::v, true>(buf, A.logP2, two ? 2 * nrows : nrows, P2, tw, I.logTW);
+        trace_mark(t, 43);
+        fft_lines<W, true>(buf, A.logP2, two ? 2 * nrows : nrows, P2, wk.tw);
+        trace_mark(t, 44);
         for (int idx = threadIdx.x; idx < nrows * P2; idx += blockDim.x) {
             const int sl = idx / P2, m2 = idx - sl * P2;
-            const cx<W> w = conj(tw[(rows[sl] * m2) << tsh]);
-            Y[(long long)rows[sl] * P2 + m2] = buf[idx] * w;
-            if (two) Y2[(long long)rows[sl] * P2 + m2] = buf2[idx] * w;
+            const cx<W> w = conj(g[(rows[sl] * m2) << tsh]);
+            Y[(long long)rows[sl] * P2 + m2] = buf[pad(idx)] * w;
+            if (two) Y2[(long long)rows[sl] * P2 + m2] = buf[pad(o2 + idx)] * w;
         }
         __syncthreads();
     }
 }
 
-// Column phase of the inverse transform: P1-point inverse FFTs of columns
-// of Y (and Y2), unpack q_m -> a_{2m}, a_{2m+1}, epilogue.
-template <typename W, bool TWO, typename EpiF>
-FDE_NI void split_inv_cols(const Team& t, const Inst& I, const cx<W>* Y, const cx<W>* Y2, unsigned char* work,
-                          int cc, EpiF epi) {
+// Inverse column transform of one unit into the buffer (both sets when two).
+template <typename W>
+FDE_D void split_inv_unit_fft(const Inst& I, const Wk& wk, const cx<W>* Y, const cx<W>* Y2, int m2b, int cc,
+                              bool two) {
     const AxisData& A = I.ax[0];
-    const int n = A.n, P1 = A.P1, P2 = A.P2;
-    const cx<W>* tw = Prec<W>::tw(I);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
-    cx<W>* buf2 = buf + cc * P1;
+    const int P1 = A.P1, P2 = A.P2;
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
+        const int c = idx % cc, j1 = idx / cc;
+        buf[pad(c * P1 + j1)] = ldw(Y + (long long)j1 * P2 + m2b + c);
+        if (two) buf[pad((cc + c) * P1 + j1)] = ldw(Y2 + (long long)j1 * P2 + m2b + c);
+    }
+    __syncthreads();
+    fft_lines<W, true>(buf, A.logP1, two ? 2 * cc : cc, P1, wk.tw);
+}
+
+// Inverse column phase: a_k (and b_k) of each unit's columns to the epilogue.
+template <typename W>
+FDE_NI void split_inv_cols(const Team& t, const Inst& I, const Wk& wk, const cx<W>* Y, const cx<W>* Y2, int cc,
+                           bool two, Epi<W> epi) {
+    const AxisData& A = I.ax[0];
+    const cx<W>* buf = reinterpret_cast<const cx<W>*>(wk.smem);
+    const int units = A.P2 / cc;
+    for (int un = t.rank; un < units; un += t.size) {
+        const int m2b = un * cc;
+        split_inv_unit_fft<W>(I, wk, Y, Y2, m2b, cc, two);
+        const int total = (A.P1 / 2) * cc * 2;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int m1 = idx / (2 * cc);
+            const int rem = idx - m1 * 2 * cc;
+            const int c = rem >> 1, e = rem & 1;
+            const long long k = 2LL * (A.P2 * m1 + m2b + c) + e;
+            if (k >= 1 && k <= A.n) {
+                const cx<W> q = buf[pad(c * A.P1 + m1)];
+                W vb = W(0);
+                if (two) {
+                    const cx<W> q2 = buf[pad((cc + c) * A.P1 + m1)];
+                    vb = e ? q2.y : q2.x;
+                }
+                epi(k - 1, e ? q.y : q.x, vb);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// tau inverse columns -> z (written to zout) -> matvec forward columns on the
+// same units: the zero-padded packing of z at m = P2 m1 + m2 takes exactly
+// the tau outputs k = 2m, 2m+1 of column m2.
+template <typename W>
+FDE_NI void split_tau_inv_mv_fwd(const Team& t, const Inst& I, const Wk& wk, const cx<W>* Yt, cx<W>* Ym, int cc,
+                                 W* zout) {
+    const AxisData& A = I.ax[0];
+    const int P1 = A.P1, P2 = A.P2, n = A.n;
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    const W* dinv = Prec<W>::dinv(I);
+    const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;
     const int units = P2 / cc;
-    for (int u = t.rank; u < units; u += t.size) {
-        const int m2b = u * cc;
+    const int tsh = wk.tw.logTW - A.logNp;
+    const cx<W>* g = tw_global_table<W>(wk.tw);
+    for (int un = t.rank; un < units; un += t.size) {
+        const int m2b = un * cc;
+        split_inv_unit_fft<W>(I, wk, Yt, nullptr, m2b, cc, false);
+        for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
+            const int c = idx / P1, m1 = idx - c * P1;
+            const long long m = (long long)P2 * m1 + m2b + c;
+            const cx<W> q = buf[pad(idx)];
+            W zr[2] = {W(0), W(0)};
+            if (m1 < P1 / 2) {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const long long k = 2 * m + e;
+                    if (k >= 1 && k <= n) {
+                        W v = e ? q.y : q.x;
+                        if (post) v *= __ldg(dinv + (k - 1));
+                        zout[k - 1] = v;
+                        zr[e] = v;
+                    }
+                }
+            }
+            buf[pad(idx)] = mk(zr[0], zr[1]);
+        }
+        __syncthreads();
+        fft_lines<W, false>(buf, A.logP1, cc, P1, wk.tw);
         for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
             const int c = idx % cc, j1 = idx / cc;
-            buf[c * P1 + j1] = ldw(Y + (long long)j1 * P2 + m2b + c);
-            if (TWO) buf2[c * P1 + j1] = ldw(Y2 + (long long)j1 * P2 + m2b + c);
-        }
-        __syncthreads();
-        fft_inplace<W, Ept<W>::v, true>(buf, A.logP1, TWO ? 2 * cc : cc, P1, tw, I.logTW);
-        for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
-            const int c = idx % cc, m1 = idx / cc;
-            const long long m = (long long)P2 * m1 + m2b + c;
-            const cx<W> q = buf[c * P1 + m1];
-            const cx<W> q2 = TWO ? buf2[c * P1 + m1] : czero<W>();
-            const long long k0 = 2 * m, k1 = 2 * m + 1;       // a_k for k = 1..n
-            if (k0 >= 1 && k0 <= n) epi(k0 - 1, q.x, q2.x);
-            if (k1 <= n) epi(k1 - 1, q.y, q2.y);
+            const int m2 = m2b + c;
+            Ym[(long long)j1 * P2 + m2] = buf[pad(c * P1 + j1)] * g[(j1 * m2) << tsh];
         }
         __syncthreads();
     }
-}
-
-template <typename W>
-FDE_NI bool split_matvec_1d(const Team& t, const Inst& I, const W* x, W s, W* y, unsigned char* work, int bytes) {
-    const AxisData& A = I.ax[0];
-    const bool sym = I.symx;
-    cx<W>* Y = Prec<W>::split(I);
-    cx<W>* Y2 = Y + A.Np;
-    const RealIn<W> in{x, 1, s, nullptr};
-    const int cc1 = split_cols_per_unit<W>(A, t.size, 1, bytes);
-    split_fwd_cols<W, kExtZero>(t, I, in, Y, work, cc1);
-    if (!team_sync(t)) return false;
-    split_rows<W>(t, I, mult_matvec<W>(A, sym), Y, Y2, work);
-    if (!team_sync(t)) return false;
-    const W c0s = W(I.c0) * s;
-    const W* dp = Prec<W>::dp(I);
-    const W* dm = Prec<W>::dm(I);
-    if (sym) {
-        split_inv_cols<W, false>(t, I, Y, Y2, work, cc1, [&](long long p, W va, W) {
-            y[p] = c0s * ldw(x + p) + coef(dp, I.dpc, p) * va;
-        });
-    } else {
-        const int cc2 = split_cols_per_unit<W>(A, t.size, 2, bytes);
-        split_inv_cols<W, true>(t, I, Y, Y2, work, cc2, [&](long long p, W va, W vb) {
-            y[p] = c0s * ldw(x + p) + coef(dp, I.dpc, p) * va + coef(dm, I.dmc, p) * vb;
-        });
-    }
-    return true;
-}
-
-template <typename W>
-FDE_NI bool split_tau_1d(const Team& t, const Inst& I, const W* r, W s, W* z, unsigned char* work, int bytes) {
-    const AxisData& A = I.ax[0];
-    cx<W>* Y = Prec<W>::split(I);
-    const W* dinv = Prec<W>::dinv(I);
-    const bool pre = I.has_D && I.order == FDE_ORDER_D_TAU;
-    const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;
-    const RealIn<W> in{r, 1, s, pre ? dinv : nullptr};
-    const int cc = split_cols_per_unit<W>(A, t.size, 1, bytes);
-    split_fwd_cols<W, kExtOdd>(t, I, in, Y, work, cc);
-    if (!team_sync(t)) return false;
-    split_rows<W>(t, I, mult_tau1<W>(A), Y, nullptr, work);
-    if (!team_sync(t)) return false;
-    split_inv_cols<W, false>(t, I, Y, nullptr, work, cc, [&](long long p, W va, W) {
-        z[p] = post ? va * __ldg(dinv + p) : va;
-    });
-    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -307,40 +460,30 @@ FDE_NI bool split_tau_1d(const Team& t, const Inst& I, const W* r, W s, W* z, un
 // ---------------------------------------------------------------------------
 
 template <typename W>
-FDE_D int plane_lines_per_unit(int Np, int nbuf, int nlines_total, int team_size, int bytes, int extra_real) {
-    // extra_real: bytes of a real Np-array per line kept beside the buffers
-    int cap = max_lines<W>(Np, nbuf, bytes - 64);
-    if (extra_real) {
-        const int per = (int)(Np * (nbuf * sizeof(cx<W>) + sizeof(W)));
-        const int c2 = bytes / per;
-        if (c2 < cap) cap = c2;
-    }
-    int want = (nlines_total + team_size - 1) / team_size;
+FDE_HD int plane_lines_per_unit(int Np, int nbuf, int nlines_total, int team_size, int bytes, int extra_real) {
+    const int cap = max_lines<W>(Np, nbuf, bytes, extra_real);
+    const int want = (nlines_total + team_size - 1) / team_size;
     int b = want < cap ? want : cap;
-    if (b < 1) b = 1;
-    return b;
+    return b < 1 ? 1 : b;
 }
 
-// Lone DST-I along rows: out[row, j-1] = s_j of (scale * in[row, :]) (* pre),
-// multiplied by post[row, j-1] when post != null.
+// Lone DST-I along rows: out[row, j-1] = s_j (* post) of the rows of u.
 template <typename W>
-FDE_NI void plane_dst_rows(const Team& t, const Inst& I, const W* in, W s, const W* pre, const W* post, W* out,
-                          unsigned char* work, int bytes) {
+FDE_NI void plane_dst_rows(const Team& t, const Inst& I, const Wk& wk, Combo<W> u, const W* post, W* out) {
     const AxisData& A = I.ax[0];
     const int n1 = A.n, Np = A.Np, n2 = I.n2;
-    const int B = plane_lines_per_unit<W>(Np, 1, n2, t.size, bytes, 1);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
-    W* sv = reinterpret_cast<W*>(buf + B * Np);
+    const int B = plane_lines_per_unit<W>(Np, 1, n2, t.size, wk.bytes, 1);
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    W* sv = reinterpret_cast<W*>(buf + padded_len(B * Np));
     const int units = (n2 + B - 1) / B;
-    for (int u = t.rank; u < units; u += t.size) {
-        const int row0 = u * B;
+    for (int un = t.rank; un < units; un += t.size) {
+        const int row0 = un * B;
         const int nb = (n2 - row0) < B ? (n2 - row0) : B;
-        cta_pack<W, kExtOdd, false>(buf, nb, n1, Np, [&](int l) {
-            const long long o = (long long)(row0 + l) * n1;
-            return RealIn<W>{in + o, 1, s, pre ? pre + o : nullptr};
+        cta_pack<W, kExtOdd, false>(buf, nb, n1, Np, [&](int l, int k, bool d) {
+            return u.get((long long)(row0 + l) * n1 + (k - 1), d);
         });
-        fft_inplace<W, Ept<W>::v, false>(buf, A.logNp, nb, Np, Prec<W>::tw(I), I.logTW);
-        cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, Prec<W>::tw(I), I.logTW);
+        fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
+        cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
         for (int idx = threadIdx.x; idx < nb * n1; idx += blockDim.x) {
             const int l = idx / n1, p = idx - l * n1;
             const long long o = (long long)(row0 + l) * n1 + p;
@@ -354,149 +497,273 @@ FDE_NI void plane_dst_rows(const Team& t, const Inst& I, const W* in, W s, const
 
 // tau^{-1} along columns in place: z[:, c] <- S2 diag(phi) S2 z[:, c].
 template <typename W>
-FDE_NI void plane_tau_cols(const Team& t, const Inst& I, W* z, unsigned char* work, int bytes) {
+FDE_NI void plane_tau_cols(const Team& t, const Inst& I, const Wk& wk, W* z) {
     const AxisData& A = I.ax[1];
     const int n2 = A.n, Np = A.Np, n1 = I.n1;
-    const int C = plane_lines_per_unit<W>(Np, 1, n1, t.size, bytes, 0);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
+    const int C = plane_lines_per_unit<W>(Np, 1, n1, t.size, wk.bytes, 0);
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const Mult<W> mu = mult_tau2<W>(I);
     const int units = (n1 + C - 1) / C;
-    for (int u = t.rank; u < units; u += t.size) {
-        const int c0 = u * C;
+    for (int un = t.rank; un < units; un += t.size) {
+        const int c0 = un * C;
         const int nc = (n1 - c0) < C ? (n1 - c0) : C;
-        cta_pack<W, kExtOdd, true>(buf, nc, n2, Np, [&](int l) {
-            return RealIn<W>{z + c0 + l, n1, W(1), nullptr};
+        cta_pack<W, kExtOdd, true>(buf, nc, n2, Np, [&](int l, int k, bool) {
+            return ldw(z + (long long)(k - 1) * n1 + c0 + l);
         });
-        fft_inplace<W, Ept<W>::v, false>(buf, A.logNp, nc, Np, Prec<W>::tw(I), I.logTW);
-        cta_spectral<W>(buf, nullptr, nc, Np, A.logNp, Prec<W>::tw(I), I.logTW, mu,
-                        [&](int l) { return c0 + l; });
-        fft_inplace<W, Ept<W>::v, true>(buf, A.logNp, nc, Np, Prec<W>::tw(I), I.logTW);
-        cta_unpack<W, true, false>(buf, nullptr, nc, n2, Np, [&](int l, int p, W va, W) {
+        fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
+        cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [&](int l) { return c0 + l; });
+        fft_lines<W, true>(buf, A.logNp, nc, Np, wk.tw);
+        cta_unpack<W, true, false>(buf, nc, n2, Np, [&](int l, int p, W va, W) {
             z[(long long)p * n1 + c0 + l] = va;
         });
         __syncthreads();
     }
 }
 
-// x part of the matvec: tmp = c0 s x + D_+ (I (x) T_a)(s x) + D_- (I (x) T_a^T)(s x).
+// x part of the matvec on the rows of s x; epi(o, a, b).
 template <typename W>
-FDE_NI void plane_matvec_rows(const Team& t, const Inst& I, const W* x, W s, W* tmp, unsigned char* work,
-                             int bytes) {
+FDE_NI void plane_matvec_rows(const Team& t, const Inst& I, const Wk& wk, const W* x, W s, Epi<W> epi) {
     const AxisData& A = I.ax[0];
     const int n1 = A.n, Np = A.Np, n2 = I.n2;
     const bool sym = I.symx;
-    const int B = plane_lines_per_unit<W>(Np, sym ? 1 : 2, n2, t.size, bytes, 0);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
+    const int B = plane_lines_per_unit<W>(Np, sym ? 1 : 2, n2, t.size, wk.bytes, 0);
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const Mult<W> mu = mult_matvec<W>(A, sym);
-    const W c0s = W(I.c0) * s;
-    const W* dp = Prec<W>::dp(I);
-    const W* dm = Prec<W>::dm(I);
     const int units = (n2 + B - 1) / B;
-    for (int u = t.rank; u < units; u += t.size) {
-        const int row0 = u * B;
+    for (int un = t.rank; un < units; un += t.size) {
+        const int row0 = un * B;
         const int nb = (n2 - row0) < B ? (n2 - row0) : B;
-        cx<W>* buf2 = buf + nb * Np;
-        cta_pack<W, kExtZero, false>(buf, nb, n1, Np, [&](int l) {
-            return RealIn<W>{x + (long long)(row0 + l) * n1, 1, s, nullptr};
+        cta_pack<W, kExtZero, false>(buf, nb, n1, Np, [&](int l, int k, bool) {
+            return s * ldw(x + (long long)(row0 + l) * n1 + (k - 1));
         });
-        fft_inplace<W, Ept<W>::v, false>(buf, A.logNp, nb, Np, Prec<W>::tw(I), I.logTW);
-        cta_spectral<W>(buf, buf2, nb, Np, A.logNp, Prec<W>::tw(I), I.logTW, mu, [](int) { return 0; });
-        fft_inplace<W, Ept<W>::v, true>(buf, A.logNp, sym ? nb : 2 * nb, Np, Prec<W>::tw(I), I.logTW);
+        fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
+        cta_spectral<W>(buf, nb, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
+        fft_lines<W, true>(buf, A.logNp, sym ? nb : 2 * nb, Np, wk.tw);
         if (sym) {
-            cta_unpack<W, false, false>(buf, buf2, nb, n1, Np, [&](int l, int p, W va, W) {
-                const long long o = (long long)(row0 + l) * n1 + p;
-                tmp[o] = c0s * ldw(x + o) + coef(dp, I.dpc, o) * va;
+            cta_unpack<W, false, false>(buf, nb, n1, Np, [&](int l, int p, W va, W vb) {
+                epi((long long)(row0 + l) * n1 + p, va, vb);
             });
         } else {
-            cta_unpack<W, false, true>(buf, buf2, nb, n1, Np, [&](int l, int p, W va, W vb) {
-                const long long o = (long long)(row0 + l) * n1 + p;
-                tmp[o] = c0s * ldw(x + o) + coef(dp, I.dpc, o) * va + coef(dm, I.dmc, o) * vb;
+            cta_unpack<W, false, true>(buf, nb, n1, Np, [&](int l, int p, W va, W vb) {
+                epi((long long)(row0 + l) * n1 + p, va, vb);
             });
         }
         __syncthreads();
     }
 }
 
-// y part: y = tmp + sr [E_+ (T_b (x) I)(s x) + E_- (T_b^T (x) I)(s x)].
+// The second sine transform of the 2D tau solve (rows of tprime, D^{-1}
+// after it per the order) fused with the x part of the matvec on the same
+// rows: z is written (the y part needs it) and tmp = c0 z + D_+ T z + D_- T^T z.
 template <typename W>
-FDE_NI void plane_matvec_cols(const Team& t, const Inst& I, const W* x, W s, const W* tmp, W* y,
-                             unsigned char* work, int bytes) {
+FDE_NI void plane_dst_matvec_rows(const Team& t, const Inst& I, const Wk& wk, const W* tprime, W* z, W* tmp) {
+    const AxisData& A = I.ax[0];
+    const int n1 = A.n, Np = A.Np, n2 = I.n2;
+    const bool sym = I.symx;
+    const int nbuf = sym ? 1 : 2;
+    const int B = plane_lines_per_unit<W>(Np, nbuf, n2, t.size, wk.bytes, 1);
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    W* sv = reinterpret_cast<W*>(buf + padded_len(nbuf * B * Np));
+    const W* dinv = Prec<W>::dinv(I);
+    const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;
+    const Mult<W> mu = mult_matvec<W>(A, sym);
+    const W c0 = W(I.c0);
+    const W* dp = Prec<W>::dp(I);
+    const W* dm = Prec<W>::dm(I);
+    const int units = (n2 + B - 1) / B;
+    for (int un = t.rank; un < units; un += t.size) {
+        const int row0 = un * B;
+        const int nb = (n2 - row0) < B ? (n2 - row0) : B;
+        cta_pack<W, kExtOdd, false>(buf, nb, n1, Np, [&](int l, int k, bool) {
+            return ldw(tprime + (long long)(row0 + l) * n1 + (k - 1));
+        });
+        fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
+        cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
+        for (int idx = threadIdx.x; idx < nb * n1; idx += blockDim.x) {
+            const int l = idx / n1, p = idx - l * n1;
+            const long long o = (long long)(row0 + l) * n1 + p;
+            W v = sv[l * Np + p + 1];
+            if (post) v *= __ldg(dinv + o);
+            sv[l * Np + p + 1] = v;
+            z[o] = v;
+        }
+        __syncthreads();
+        cta_pack<W, kExtZero, false>(buf, nb, n1, Np, [&](int l, int k, bool) { return sv[l * Np + k]; });
+        fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
+        cta_spectral<W>(buf, nb, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
+        fft_lines<W, true>(buf, A.logNp, nbuf * nb, Np, wk.tw);
+        auto epi = [&](int l, int p, W va, W vb) {
+            const long long o = (long long)(row0 + l) * n1 + p;
+            W v = c0 * sv[l * Np + p + 1] + coef(dp, I.dpc, o) * va;
+            if (!sym) v += coef(dm, I.dmc, o) * vb;
+            tmp[o] = v;
+        };
+        if (sym) cta_unpack<W, false, false>(buf, nb, n1, Np, epi);
+        else cta_unpack<W, false, true>(buf, nb, n1, Np, epi);
+        __syncthreads();
+    }
+}
+
+// y part: epi(o, a, b) with a, b the T_b and T_b^T (or symmetric) products
+// of the columns of s x.  Column units of C columns; a CTA owns its units'
+// columns.
+template <typename W>
+FDE_HD int plane_cols_per_unit(const Inst& I, int team_size, int bytes) {
+    const bool sym = I.symy;
+    const int Np = I.ax[1].Np;
+    const int cap = max_lines<W>(Np, sym ? 1 : 2, bytes);
+    const int want = (I.n1 + team_size - 1) / team_size;
+    int b = want < cap ? want : cap;
+    return b < 1 ? 1 : b;
+}
+
+template <typename W>
+FDE_NI void plane_matvec_cols(const Team& t, const Inst& I, const Wk& wk, const W* x, W s, Epi<W> epi) {
     const AxisData& A = I.ax[1];
     const int n2 = A.n, Np = A.Np, n1 = I.n1;
     const bool sym = I.symy;
-    const int C = plane_lines_per_unit<W>(Np, sym ? 1 : 2, n1, t.size, bytes, 0);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(work);
+    const int C = plane_cols_per_unit<W>(I, t.size, wk.bytes);
+    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const Mult<W> mu = mult_matvec<W>(A, sym);
-    const W sr = W(I.sr);
-    const W* ep = Prec<W>::ep(I);
-    const W* em = Prec<W>::em(I);
+    const int units = (n1 + C - 1) / C;
+    for (int un = t.rank; un < units; un += t.size) {
+        const int c0 = un * C;
+        const int nc = (n1 - c0) < C ? (n1 - c0) : C;
+        cta_pack<W, kExtZero, true>(buf, nc, n2, Np, [&](int l, int k, bool) {
+            return s * ldw(x + (long long)(k - 1) * n1 + c0 + l);
+        });
+        fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
+        cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
+        fft_lines<W, true>(buf, A.logNp, sym ? nc : 2 * nc, Np, wk.tw);
+        if (sym) {
+            cta_unpack<W, true, false>(buf, nc, n2, Np, [&](int l, int p, W va, W vb) {
+                epi((long long)p * n1 + c0 + l, va, vb);
+            });
+        } else {
+            cta_unpack<W, true, true>(buf, nc, n2, Np, [&](int l, int p, W va, W vb) {
+                epi((long long)p * n1 + c0 + l, va, vb);
+            });
+        }
+        __syncthreads();
+    }
+}
+
+// Elements of the column units a CTA owns in plane_matvec_cols.
+template <typename W, typename F>
+FDE_D void plane_cols_own_elements(const Team& t, const Inst& I, int bytes, F f) {
+    const int C = plane_cols_per_unit<W>(I, t.size, bytes);
+    const int n1 = I.n1, n2 = I.n2;
     const int units = (n1 + C - 1) / C;
     for (int u = t.rank; u < units; u += t.size) {
         const int c0 = u * C;
         const int nc = (n1 - c0) < C ? (n1 - c0) : C;
-        cx<W>* buf2 = buf + nc * Np;
-        cta_pack<W, kExtZero, true>(buf, nc, n2, Np, [&](int l) {
-            return RealIn<W>{x + c0 + l, n1, s, nullptr};
-        });
-        fft_inplace<W, Ept<W>::v, false>(buf, A.logNp, nc, Np, Prec<W>::tw(I), I.logTW);
-        cta_spectral<W>(buf, buf2, nc, Np, A.logNp, Prec<W>::tw(I), I.logTW, mu, [](int) { return 0; });
-        fft_inplace<W, Ept<W>::v, true>(buf, A.logNp, sym ? nc : 2 * nc, Np, Prec<W>::tw(I), I.logTW);
-        if (sym) {
-            cta_unpack<W, true, false>(buf, buf2, nc, n2, Np, [&](int l, int p, W va, W) {
-                const long long o = (long long)p * n1 + c0 + l;
-                y[o] = ldw(tmp + o) + sr * coef(ep, I.epc, o) * va;
-            });
-        } else {
-            cta_unpack<W, true, true>(buf, buf2, nc, n2, Np, [&](int l, int p, W va, W vb) {
-                const long long o = (long long)p * n1 + c0 + l;
-                y[o] = ldw(tmp + o) + sr * (coef(ep, I.epc, o) * va + coef(em, I.emc, o) * vb);
-            });
+        for (int idx = threadIdx.x; idx < nc * n2; idx += blockDim.x) {
+            const int l = idx % nc, r = idx / nc;
+            f((long long)r * n1 + c0 + l);
         }
-        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// Dispatch.  `tmp` is an N-vector of scratch (2D matvec only).
+// Operators (team barrier at the end)
 // ---------------------------------------------------------------------------
 
+// y = M (s x), written per `o`.  `tmp`: N-vector of scratch (2D only).
 template <typename W>
-FDE_D bool op_matvec(const Team& t, const Inst& I, int line_mode, const W* x, W s, W* y, W* tmp,
-                     unsigned char* work, int bytes) {
+FDE_D bool op_matvec_out(const Team& t, const Inst& I, int line_mode, const W* x, W s, W* tmp, OutSpec<W> o,
+                         const Wk& wk) {
+    trace_mark(t, 10);
     if (I.dim == 1) {
+        const Epi<W> e = epi_mvx<W>(I, x, s, o);
         if (line_mode == kLineCta) {
-            if (t.rank == 0) cta_matvec_1d<W>(I, x, s, y, work);
+            if (t.rank == 0) cta_matvec_1d<W>(I, wk, x, s, e);
         } else {
-            if (!split_matvec_1d<W>(t, I, x, s, y, work, bytes)) return false;
+            const AxisData& A = I.ax[0];
+            cx<W>* Y = Prec<W>::split(I);
+            const int cc = split_cols_per_unit<W>(A, t.size, wk.bytes);
+            split_fwd_cols<W, kExtZero>(t, I, wk, combo_vec<W>(x, s), Y, cc);
+            if (!team_sync(t)) return false;
+            trace_mark(t, 11);
+            split_rows<W>(t, I, wk, mult_matvec<W>(A, I.symx), Y, Y + A.Np);
+            if (!team_sync(t)) return false;
+            trace_mark(t, 12);
+            split_inv_cols<W>(t, I, wk, Y, Y + A.Np, cc, !I.symx, e);
         }
     } else {
-        plane_matvec_rows<W>(t, I, x, s, tmp, work, bytes);
+        plane_matvec_rows<W>(t, I, wk, x, s, epi_mvx<W>(I, x, s, out_store<W>(tmp)));
         if (!team_sync(t)) return false;
-        plane_matvec_cols<W>(t, I, x, s, tmp, y, work, bytes);
+        trace_mark(t, 11);
+        plane_matvec_cols<W>(t, I, wk, x, s, epi_mvy<W>(I, tmp, o));
     }
-    return team_sync(t);
+    const bool ok = team_sync(t);
+    trace_mark(t, 13);
+    return ok;
 }
 
 template <typename W>
-FDE_D bool op_tau(const Team& t, const Inst& I, int line_mode, const W* r, W s, W* z, unsigned char* work,
-                  int bytes) {
+FDE_D bool op_matvec(const Team& t, const Inst& I, int line_mode, const W* x, W s, W* y, W* tmp, const Wk& wk) {
+    return op_matvec_out<W>(t, I, line_mode, x, s, tmp, out_store<W>(y), wk);
+}
+
+// z = P^{-1} u, u given by a Combo; written per `o`.  `zbuf`: an N-vector the
+// 2D path uses in place (it may be o.out).
+template <typename W>
+FDE_D bool op_tau_combo(const Team& t, const Inst& I, int line_mode, Combo<W> u, W* zbuf, OutSpec<W> o,
+                        const Wk& wk) {
+    trace_mark(t, 20);
+    const W* dinv = Prec<W>::dinv(I);
+    const bool pre = I.has_D && I.order == FDE_ORDER_D_TAU;
+    const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;
     if (I.dim == 1) {
         if (line_mode == kLineCta) {
-            if (t.rank == 0) cta_tau_1d<W>(I, r, s, z, work);
+            if (t.rank == 0) cta_tau_1d<W>(I, wk, u, epi_a<W>(nullptr, o));
         } else {
-            if (!split_tau_1d<W>(t, I, r, s, z, work, bytes)) return false;
+            const AxisData& A = I.ax[0];
+            cx<W>* Y = Prec<W>::split(I);
+            if (pre) u.pre = dinv;
+            const int cc = split_cols_per_unit<W>(A, t.size, wk.bytes);
+            split_fwd_cols<W, kExtOdd>(t, I, wk, u, Y, cc);
+            if (!team_sync(t)) return false;
+            trace_mark(t, 21);
+            split_rows<W>(t, I, wk, mult_tau1<W>(A), Y, nullptr);
+            if (!team_sync(t)) return false;
+            trace_mark(t, 22);
+            split_inv_cols<W>(t, I, wk, Y, nullptr, cc, false, epi_a<W>(post ? dinv : nullptr, o));
         }
     } else {
-        const W* dinv = Prec<W>::dinv(I);
-        const bool pre = I.has_D && I.order == FDE_ORDER_D_TAU;
-        const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;
-        plane_dst_rows<W>(t, I, r, s, pre ? dinv : nullptr, nullptr, z, work, bytes);
+        if (pre) u.pre = dinv;
+        plane_dst_rows<W>(t, I, wk, u, nullptr, zbuf);
         if (!team_sync(t)) return false;
-        plane_tau_cols<W>(t, I, z, work, bytes);
+        trace_mark(t, 21);
+        plane_tau_cols<W>(t, I, wk, zbuf);
         if (!team_sync(t)) return false;
-        plane_dst_rows<W>(t, I, z, W(1), nullptr, post ? dinv : nullptr, z, work, bytes);
+        trace_mark(t, 22);
+        // last sine transform along rows; a row belongs to one CTA, so reading
+        // zbuf and writing the output (possibly zbuf) is safe
+        if (o.outk == kOutStore) {
+            plane_dst_rows<W>(t, I, wk, combo_vec<W>(zbuf, W(1)), post ? dinv : nullptr, o.out);
+        } else {
+            // out += z: z first into zbuf (row-local), then the update of the same rows
+            plane_dst_rows<W>(t, I, wk, combo_vec<W>(zbuf, W(1)), post ? dinv : nullptr, zbuf);
+            __syncthreads();
+            const int B = plane_lines_per_unit<W>(I.ax[0].Np, 1, I.n2, t.size, wk.bytes, 1);
+            const int units = (I.n2 + B - 1) / B;
+            const Epi<W> e = epi_a<W>(nullptr, o);
+            for (int un = t.rank; un < units; un += t.size) {
+                const long long o0 = (long long)un * B * I.n1;
+                const long long o1 = (long long)((un + 1) * B < I.n2 ? (un + 1) * B : I.n2) * I.n1;
+                for (long long p = o0 + threadIdx.x; p < o1; p += blockDim.x) e(p, ldw(zbuf + p), W(0));
+            }
+        }
     }
-    return team_sync(t);
+    const bool ok = team_sync(t);
+    trace_mark(t, 23);
+    return ok;
+}
+
+template <typename W>
+FDE_D bool op_tau(const Team& t, const Inst& I, int line_mode, const W* r, W s, W* z, const Wk& wk) {
+    return op_tau_combo<W>(t, I, line_mode, combo_vec(r, s), z, out_store<W>(z), wk);
 }
 
 }  // namespace fde

@@ -18,7 +18,24 @@ struct Team {
     unsigned int* gen;
     double* partial;       // [size][kMaxDots]
     unsigned int* abort_flag;
+    SyncArea* sync;
 };
+
+// Phase timestamps for performance analysis (compiled in with -DFDE_TRACE):
+// CTA 0 of the launch appends (code, %globaltimer) pairs to the sync area.
+FDE_D void trace_mark(const Team& t, int code) {
+#ifdef FDE_TRACE
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long ns;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
+        const unsigned int i = atomicAdd(&t.sync->trace_n, 1u);
+        if (i < (unsigned)kTraceEntries) t.sync->trace[i] = ((unsigned long long)code << 48) | (ns & 0xffffffffffffULL);
+    }
+#else
+    (void)t;
+    (void)code;
+#endif
+}
 
 FDE_D unsigned int ld_volatile(const unsigned int* p) {
     return *reinterpret_cast<const volatile unsigned int*>(p);
@@ -76,6 +93,56 @@ FDE_D void block_sum(const double (&v)[K], double* out, double* scratch /* [K*32
     for (int k = 0; k < K; ++k) {
         const double s = warp_sum(v[k]);
         if (lane == 0) scratch[k * 32 + warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += scratch[threadIdx.x * 32 + w];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Compensated FP32 accumulation (for FP32 vectors): the product a*b is split
+// exactly into p + e with one FMA, the running sum s absorbs p through an
+// error-free TwoSum, and both rounding errors collect in c.  (s + c) carries
+// roughly twice the FP32 precision -- FP64-class inner products without the
+// FP64 pipe, which on this GPU issues at a small fraction of the FP32 rate.
+struct F2 {
+    float s, c;
+};
+
+FDE_D void two_sum_acc(F2& a, float p) {
+    const float t = a.s + p;
+    const float bp = t - a.s;
+    a.c += (a.s - (t - bp)) + (p - bp);
+    a.s = t;
+}
+
+FDE_D void dot2_acc(F2& a, float x, float y) {
+    const float p = x * y;
+    const float e = fmaf(x, y, -p);
+    two_sum_acc(a, p);
+    a.c += e;
+}
+
+// Block-wide sums of K compensated FP32 values: warp trees in pairs, then
+// FP64 across warps.  out[0..K) in shared memory.
+template <int K>
+FDE_D void block_sum_f2(const F2 (&v)[K], double* out, double* scratch /* [K*32] smem */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        F2 a = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, a.s, o);
+            const float oc = __shfl_xor_sync(0xffffffffu, a.c, o);
+            two_sum_acc(a, os);
+            a.c += oc;
+        }
+        if (lane == 0) scratch[k * 32 + warp] = (double)a.s + (double)a.c;
     }
     __syncthreads();
     if (threadIdx.x < K) {
