@@ -165,6 +165,41 @@ fde_status fde_krylov_solve(const fde_plan* const* plans, int count, const doubl
 fde_status fde_step_rhs(const fde_plan* plan, const double* u_prev, const double* f,
                         double* b, void* stream);
 
+/*
+ * y = M x for a 1D problem (Sec. 1.2, eq. for M_{alpha,n}: c0 x + D_+ T x +
+ * D_- T^T x, T applied by 2(n+1)-circulant embedding and FFT), in FP64, with
+ * no plan, no workspace and no allocation.  The paper has no counterpart of
+ * this entry point: it gives callers that cannot allocate device memory a
+ * product with M.  Such callers are, for instance, a time-stepping code whose
+ * device memory is held by another allocator (a caching allocator such as
+ * PyTorch's may have reserved nearly all of it, so cudaMalloc fails), or a
+ * loop with work in flight on other streams (cudaFree synchronises the whole
+ * device and would stall them).
+ *
+ * The symbol data (twiddles, weights g_k or w_k, circulant eigenvalues) and
+ * the transform buffers live in one fixed static device array of
+ * FDE_MATVEC_NOALLOC_SCRATCH_BYTES bytes, sized for n1 <= FDE_MATVEC_NOALLOC_MAX_N.
+ *   prob: 1D problem as for fde_assemble_symbol (coefficient arrays device
+ *         FP64 or NULL for the constants; tau_shift and order are ignored).
+ *   x, y: device FP64 arrays of n1 elements, x != y; the caller owns them.
+ * Errors (nothing is launched): NULL prob/x/y, x == y, dim != 1 or an invalid
+ * problem -> FDE_EINVAL; n1 > FDE_MATVEC_NOALLOC_MAX_N -> FDE_ENOMEM (the
+ * problem does not fit the fixed scratch).  FDE_ECUDA if setup or a launch
+ * fails.
+ * Setup: the first call on each device (made with that device current)
+ * resolves the scratch's device address once; make that first call before
+ * any stream capture.
+ * No part of the scratch needs to start at zero: every call writes each
+ * scratch word it reads before reading it.
+ * Calls that overlap in time on one device (on different streams, or from
+ * different host threads) share the scratch and race; order them on one
+ * stream.  Three single-CTA launches on `stream`: meant for occasional
+ * products; the solvers use fde_toeplitz_matvec with a plan.
+ */
+#define FDE_MATVEC_NOALLOC_MAX_N 4095
+#define FDE_MATVEC_NOALLOC_SCRATCH_BYTES 640256
+fde_status fde_toeplitz_matvec_noalloc(const fde_problem* prob, const double* x, double* y, void* stream);
+
 /* Scalars the plan derived from the problem: c0, sr, h1^alpha. */
 fde_status fde_plan_scalars(const fde_plan* plan, double* c0, double* sr, double* h_alpha);
 

@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
         L.fde_assemble_symbol.restype = cint
         L.fde_toeplitz_matvec.argtypes = [vp, cint, vp, vp, vp]
         L.fde_toeplitz_matvec.restype = cint
+        L.fde_toeplitz_matvec_noalloc.argtypes = [P(FdeProblem), vp, vp, vp]
+        L.fde_toeplitz_matvec_noalloc.restype = cint
         L.fde_tau_solve.argtypes = [vp, cint, vp, vp, vp]
         L.fde_tau_solve.restype = cint
         L.fde_krylov_solve.argtypes = [P(vp), cint, P(vp), P(vp), P(FdeSolveOpts), vp, vp]
@@ -187,6 +189,17 @@ def assemble_symbol(problem: FdeProblem, opts: FdeSolveOpts, workspace, nbytes: 
 
 def toeplitz_matvec(plan: int, dtype: int, x, y, stream=None):
     _check(lib().fde_toeplitz_matvec(plan, dtype, _ptr(x), _ptr(y), _stream(stream)), "fde_toeplitz_matvec")
+
+
+MATVEC_NOALLOC_MAX_N = 4095
+
+
+def toeplitz_matvec_noalloc(problem: FdeProblem, x, y, stream=None):
+    """y = M x for a 1D problem without a plan or workspace (FP64, n1 <= 4095);
+    the library's fixed static scratch holds the symbol data.  Calls that
+    overlap in time on one device race on that scratch."""
+    _check(lib().fde_toeplitz_matvec_noalloc(ctypes.byref(problem), _ptr(x), _ptr(y), _stream(stream)),
+           "fde_toeplitz_matvec_noalloc")
 
 
 def tau_solve(plan: int, dtype: int, r, z, stream=None):

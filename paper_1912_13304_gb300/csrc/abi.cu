@@ -667,3 +667,186 @@ fde_status fde_step_rhs(const fde_plan* p, const double* u_prev, const double* f
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// fde_toeplitz_matvec_noalloc: y = M x for a 1D problem with its symbol data
+// and transform buffers in a fixed static device array instead of a
+// caller-provided workspace.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kNoallocMaxNp = FDE_MATVEC_NOALLOC_MAX_N + 1;   // 4096: L = 8192
+constexpr int kNoallocTW = 2 * kNoallocMaxNp;
+
+struct NoallocLayout {
+    size_t tw64, tw32, lam64, lam32, phi64, phi32, wts, buf, total;
+};
+
+constexpr NoallocLayout noalloc_layout() {
+    NoallocLayout L{};
+    size_t off = 0;
+    auto take = [&off](size_t b) { const size_t o = off; off = (off + b + kAlign - 1) & ~(kAlign - 1); return o; };
+    L.tw64 = take((size_t)kNoallocTW * sizeof(cx<double>));
+    L.tw32 = take((size_t)kNoallocTW * sizeof(cx<float>));
+    L.lam64 = take((size_t)(kNoallocMaxNp + 1) * sizeof(cx<double>));
+    L.lam32 = take((size_t)(kNoallocMaxNp + 1) * sizeof(cx<float>));
+    L.phi64 = take((size_t)(kNoallocMaxNp + 1) * sizeof(double));
+    L.phi32 = take((size_t)(kNoallocMaxNp + 1) * sizeof(float));
+    L.wts = take((size_t)(kNoallocMaxNp + 2) * sizeof(double));
+    L.buf = take((size_t)4 * kNoallocMaxNp * sizeof(cx<double>));   // two ping-pong pairs
+    L.total = off;
+    return L;
+}
+
+constexpr NoallocLayout kNoalloc = noalloc_layout();
+static_assert(kNoalloc.total == FDE_MATVEC_NOALLOC_SCRATCH_BYTES, "scratch size in fde.h is stale");
+
+}  // namespace
+
+// The scratch itself: file scope, one copy per device.
+static __device__ __align__(256) unsigned char g_matvec_scratch[FDE_MATVEC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_scratch_mu;
+unsigned char* g_scratch_ptr[64];
+
+// Device address of g_matvec_scratch on `dev` (the current device), resolved once.
+cudaError_t matvec_scratch(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+struct LineJob {
+    int n, Np, logNp, logTW;
+    double c0;
+    const double* dp;
+    const double* dm;
+    double dpc, dmc;
+    const cx<double>* tw64;
+    const cx<double>* lam;     // circulant eigenvalues / L, [Np + 1]
+    const double* x;
+    double* y;
+    cx<double>* buf;           // 4 Np complex values
+};
+
+// One CTA: the zero-extended line x (v_k = x_k for 1 <= k <= n, 0 elsewhere on
+// 0..L-1) is packed, transformed, multiplied by lambda and by conj(lambda)
+// (T x and T^T x) and transformed back; y = c0 x + d_+ T x + d_- T^T x.
+__global__ void __launch_bounds__(1024) k_line_matvec(LineJob J) {
+    const int n = J.n, Np = J.Np;
+    cx<double>* A = J.buf;
+    cx<double>* B = A + Np;
+    cx<double>* C = B + Np;
+    cx<double>* D = C + Np;
+    for (int m = threadIdx.x; m < Np; m += blockDim.x) {
+        const int k0 = 2 * m, k1 = 2 * m + 1;
+        A[m] = mk(k0 >= 1 && k0 <= n ? J.x[k0 - 1] : 0.0, k1 <= n ? J.x[k1 - 1] : 0.0);
+    }
+    __syncthreads();
+    cx<double>* Z = fft_pingpong<double, false>(A, B, J.logNp, J.tw64, J.logTW);
+    cx<double>* Zo = Z == A ? B : A;
+    const int wsh = J.logTW - (J.logNp + 1);
+    for (int j = threadIdx.x; j <= Np / 2; j += blockDim.x) {
+        const int jm = (Np - j) & (Np - 1);
+        const cx<double> wj = J.tw64[j << wsh];
+        cx<double> a, b, Qj, Qm;
+        unpack_pair(Z[j], Z[jm], wj, a, b);
+        const cx<double> lj = J.lam[j];
+        const cx<double> lm = J.lam[Np - j];
+        repack_pair(lj * a, conj(lm) * b, wj, Qj, Qm);
+        C[j] = Qj;
+        if (jm != j) C[jm] = Qm;
+        repack_pair(conj(lj) * a, lm * b, wj, Qj, Qm);
+        Zo[j] = Qj;
+        if (jm != j) Zo[jm] = Qm;
+    }
+    __syncthreads();
+    const cx<double>* R1 = fft_pingpong<double, true>(C, D, J.logNp, J.tw64, J.logTW);
+    const cx<double>* R2 = fft_pingpong<double, true>(Zo, Z, J.logNp, J.tw64, J.logTW);
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int k = p + 1;
+        const cx<double> q1 = R1[k >> 1];
+        const cx<double> q2 = R2[k >> 1];
+        const double ta = (k & 1) ? q1.y : q1.x;
+        const double tb = (k & 1) ? q2.y : q2.x;
+        const double dp = J.dp ? J.dp[p] : J.dpc;
+        const double dm = J.dm ? J.dm[p] : J.dmc;
+        J.y[p] = J.c0 * J.x[p] + dp * ta + dm * tb;
+    }
+}
+
+}  // namespace
+
+extern "C" fde_status fde_toeplitz_matvec_noalloc(const fde_problem* prob, const double* x, double* y,
+                                                  void* stream) {
+    if (!prob || !x || !y || x == y) return FDE_EINVAL;
+    const fde_problem* p = prob;
+    if (p->dim != 1 || p->n1 < 1 || !is_pow2((long long)p->n1 + 1) || !valid_order(p->alpha)) return FDE_EINVAL;
+    if (!(p->len1 > 0.0) || !std::isfinite(p->len1) || !(p->dt > 0.0) || !std::isfinite(p->dt)) return FDE_EINVAL;
+    if (p->scheme != FDE_SCHEME_IMPLICIT_EULER && p->scheme != FDE_SCHEME_CRANK_NICOLSON) return FDE_EINVAL;
+    if (p->weights != FDE_WEIGHTS_GL1 && p->weights != FDE_WEIGHTS_WSGD2) return FDE_EINVAL;
+    if (!coeff_ok(p->dp, p->dp_const) || !coeff_ok(p->dm, p->dm_const)) return FDE_EINVAL;
+    if (p->n1 > FDE_MATVEC_NOALLOC_MAX_N) return FDE_ENOMEM;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FDE_ECUDA;
+    unsigned char* s = nullptr;
+    if (matvec_scratch(dev, &s) != cudaSuccess) return FDE_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    const int Np = p->n1 + 1;
+    const int logNp = ilog2(Np);
+    const int TW = std::max(2 * Np, 16);
+    const int logTW = ilog2(TW);
+    auto tw64 = reinterpret_cast<cx<double>*>(s + kNoalloc.tw64);
+    auto lam64 = reinterpret_cast<cx<double>*>(s + kNoalloc.lam64);
+    k_twiddles<<<std::min(1024, (TW + 255) / 256), 256, 0, st>>>(tw64, reinterpret_cast<cx<float>*>(s + kNoalloc.tw32),
+                                                                 TW);
+    AxisJob J{};
+    J.n = p->n1;
+    J.Np = Np;
+    J.logNp = logNp;
+    J.logTW = logTW;
+    J.weights = p->weights;
+    J.alpha = p->alpha;
+    J.kind = 0;
+    J.add = 0.0;
+    J.mult = 1.0;
+    J.tw64 = tw64;
+    J.lam64 = lam64;
+    J.lam32 = reinterpret_cast<cx<float>*>(s + kNoalloc.lam32);
+    J.phi64 = reinterpret_cast<double*>(s + kNoalloc.phi64);
+    J.phi32 = reinterpret_cast<float*>(s + kNoalloc.phi32);
+    J.wts = reinterpret_cast<double*>(s + kNoalloc.wts);
+    J.bufA = reinterpret_cast<cx<double>*>(s + kNoalloc.buf);
+    J.bufB = J.bufA + Np;
+    k_axis<<<1, 1024, 0, st>>>(J);
+
+    LineJob M{};
+    M.n = p->n1;
+    M.Np = Np;
+    M.logNp = logNp;
+    M.logTW = logTW;
+    const double ha = std::pow(p->len1 / (p->n1 + 1), p->alpha);
+    M.c0 = (p->scheme == FDE_SCHEME_CRANK_NICOLSON ? 2.0 : 1.0) * ha / p->dt;
+    M.dp = p->dp;
+    M.dm = p->dm;
+    M.dpc = p->dp_const;
+    M.dmc = p->dm_const;
+    M.tw64 = tw64;
+    M.lam = lam64;
+    M.x = x;
+    M.y = y;
+    M.buf = reinterpret_cast<cx<double>*>(s + kNoalloc.buf);
+    k_line_matvec<<<1, 1024, 0, st>>>(M);
+    return cudaGetLastError() == cudaSuccess ? FDE_OK : FDE_ECUDA;
+}
