@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
         const int m = s_inst.method == FDE_GMRES ? s_inst.restart : 1;
         const size_t hdr = kshared_bytes(m, s_inst.logTsm);
         KShared ks = kshared_carve(dsm, m);
+        ks.wide = reinterpret_cast<double*>(dsm + hdr);
         // quarter-wave twiddle table of W_T, T = 2^logTsm, from the global table
         {
             const int q = (1 << s_inst.logTsm) >> 2;

@@ -40,6 +40,13 @@ template <typename R> FDE_D cx<R> tw_quarter_entry(const Tw& t, int r);
 template <> FDE_D cx<double> tw_quarter_entry<double>(const Tw& t, int r) { return t.q[r]; }
 template <> FDE_D cx<float> tw_quarter_entry<float>(const Tw& t, int r) { return t.q32[r]; }
 
+// Sign flip by an integer XOR of the sign bit (flip = 0 or 1), which keeps
+// the selection off the floating-point pipes.
+FDE_D double flip_sign(double v, int flip) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)flip << 63));
+}
+FDE_D float flip_sign(float v, int flip) { return __int_as_float(__float_as_int(v) ^ (flip << 31)); }
+
 // Branch-free: quadrants 1 and 3 swap the components, the first component is
 // negated in quadrants 2 and 3, the second in quadrants 1 and 2.
 template <typename R>
@@ -49,7 +56,7 @@ FDE_D cx<R> tw_quarter(const Tw& t, int idx) {
     const cx<R> w = tw_quarter_entry<R>(t, r);
     const R a = (q & 1) ? w.y : w.x;
     const R b = (q & 1) ? w.x : w.y;
-    return mk((q & 2) ? -a : a, ((q + 1) & 2) ? -b : b);
+    return mk(flip_sign(a, q >> 1), flip_sign(b, ((q + 1) >> 1) & 1));
 }
 
 // W_L^j for the real-packing step (L = 2^logL, any size): global table.

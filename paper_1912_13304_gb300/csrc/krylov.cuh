@@ -45,8 +45,9 @@ struct KShared {
     double* g;
     double* y;
     double* vs;            // 1/||v_i|| of the stored (unnormalised) basis vectors
-    double* red;           // reduction results, kMaxDots + 8
-    double* scratch;       // 8 * 32 for block_sum
+    double* red;           // reduction results, kMaxDots
+    double* sc;            // 8 scalars that thread 0 computes for the CTA (red + kMaxDots)
+    double* wide;          // block_sum transpose area: the transform work area, idle during reductions
     double* coef;          // coefficients of the next on-the-fly basis vector
     float* coef32;         // the same, for FP32 vectors
     cx<double>* twq;       // W_T^t, t < T/4
@@ -86,7 +87,9 @@ FDE_D KShared kshared_carve(unsigned char* base, int m) {
     k.g = p; p += m + 2;
     k.vs = p; p += m + 2;
     k.red = p; p += kMaxDots + 8;
-    k.scratch = p; p += 8 * 32;
+    k.sc = k.red + kMaxDots;
+    k.wide = nullptr;
+    p += 8 * 32;
     k.coef = p; p += kMaxDots + 2;
     k.coef32 = reinterpret_cast<float*>(p);
     k.twq = reinterpret_cast<cx<double>*>(base + kshared_scalar_bytes(m));
@@ -120,7 +123,7 @@ FDE_D bool dots_own(const Team& t, long long N, const W* a, const W* V, const do
                     else if (kk == cnt && norm) acc[k] += ai * ai;
                 }
             });
-            block_sum<8>(acc, ks.red + c0, ks.scratch);
+            block_sum<8>(acc, ks.red + c0, ks.wide);
         } else {
             F2 acc[8];
 #pragma unroll
@@ -134,11 +137,12 @@ FDE_D bool dots_own(const Team& t, long long N, const W* a, const W* V, const do
                     else if (kk == cnt && norm) dot2_acc(acc[k], ai, ai);
                 }
             });
-            block_sum_f2<8>(acc, ks.red + c0, ks.scratch);
+            block_sum_f2<8>(acc, ks.red + c0, ks.wide);
         }
     }
     if (threadIdx.x < cnt) ks.red[threadIdx.x] *= vs[threadIdx.x];
     __syncthreads();
+    trace_mark(t, 60);
     return team_allreduce(t, ks.red, tot);
 }
 
@@ -158,23 +162,23 @@ FDE_D bool dots_pairs(const Team& t, long long N, const W* const (&a)[K], const 
     long long lo, hi;
     team_range(t, N, lo, hi);
     if constexpr (sizeof(W) == 8) {
-        double acc[8];
+        double acc[K];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+        for (int k = 0; k < K; ++k) acc[k] = 0.0;
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
 #pragma unroll
             for (int k = 0; k < K; ++k) acc[k] += (double)ldw(a[k] + i) * (double)ldw(b[k] + i);
         }
-        block_sum<8>(acc, ks.red, ks.scratch);
+        block_sum<K>(acc, ks.red, ks.wide);
     } else {
-        F2 acc[8];
+        F2 acc[K];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = F2{0.0f, 0.0f};
+        for (int k = 0; k < K; ++k) acc[k] = F2{0.0f, 0.0f};
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
 #pragma unroll
             for (int k = 0; k < K; ++k) dot2_acc(acc[k], (float)ldw(a[k] + i), (float)ldw(b[k] + i));
         }
-        block_sum_f2<8>(acc, ks.red, ks.scratch);
+        block_sum_f2<K>(acc, ks.red, ks.wide);
     }
     return team_allreduce(t, ks.red, K);
 }
@@ -358,27 +362,31 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
             if (!arnoldi_right<W>(t, I, lm, u, j + 1, v.V, v.z, v.w, v.tt, ks, wk)) return false;
             st.iterations++;
             trace_mark(t, 30);
-            const double ww = ks.red[j + 1];
-            double hh = 0.0;
-            for (int q = 0; q <= j; ++q) hh += ks.red[q] * ks.red[q];
-            double hn2;
-            if (hh < 0.5 * ww) {
+            // Scalar work is done by thread 0 and broadcast through ks.sc: an
+            // FP64 instruction repeated by every warp costs that many times
+            // the FP64 pipe.
+            if (threadIdx.x == 0) {
+                const double ww = ks.red[j + 1];
+                double hh = 0.0;
+                for (int q = 0; q <= j; ++q) hh += ks.red[q] * ks.red[q];
                 // ||w - V h|| > ||w|| / sqrt(2) (the Daniel-Gragg-Kaufman-Stewart
-                // criterion): one classical Gram-Schmidt pass is enough,
-                // V_{j+1} = w - sum h_q vs_q V_q (formed by the next step)
-                hn2 = ww - hh;
-                __syncthreads();
-                if (threadIdx.x == 0) {
+                // criterion): one classical Gram-Schmidt pass is enough
+                const bool once = hh < 0.5 * ww;
+                ks.sc[0] = once ? 0.0 : 1.0;
+                ks.sc[1] = ww - hh;
+                if (once) {
+                    // V_{j+1} = w - sum h_q vs_q V_q (formed by the next step)
                     for (int q = 0; q <= j; ++q) {
                         ks.H[q + j * (m + 1)] = ks.red[q];
                         set_coef(ks, q, ks.red[q] * ks.vs[q]);
                     }
                 }
-            } else {
+            }
+            __syncthreads();
+            if (ks.sc[0] != 0.0) {
                 // reorthogonalise: w <- w - V h, then h2 = V^T w (V_j was stored
                 // by this step's first phase; the team barrier of the reduction
                 // made it visible)
-                __syncthreads();
                 if (threadIdx.x <= j) {
                     set_coef(ks, threadIdx.x, ks.red[threadIdx.x] * ks.vs[threadIdx.x]);
                     ks.y[threadIdx.x] = ks.red[threadIdx.x];
@@ -393,11 +401,10 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
                 __syncthreads();
                 if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
                 trace_mark(t, 31);
-                double s2 = 0.0;
-                for (int q = 0; q <= j; ++q) s2 += ks.red[q] * ks.red[q];
-                hn2 = ks.red[j + 1] - s2;
-                __syncthreads();
                 if (threadIdx.x == 0) {
+                    double s2 = 0.0;
+                    for (int q = 0; q <= j; ++q) s2 += ks.red[q] * ks.red[q];
+                    ks.sc[1] = ks.red[j + 1] - s2;
                     for (int q = 0; q <= j; ++q) {
                         ks.H[q + j * (m + 1)] = ks.y[q] + ks.red[q];
                         set_coef(ks, q, ks.red[q] * ks.vs[q]);
@@ -405,20 +412,27 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
                 }
             }
             ncoef = j + 1;
-            const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
             if (threadIdx.x == 0) {
+                const double hn2 = ks.sc[1];
+                const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
                 ks.H[(j + 1) + j * (m + 1)] = hn;
                 givens_column(ks, j, m);
                 ks.vs[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+                const double est = fabs(ks.g[j + 1]);
+                const double diag = ks.H[j + j * (m + 1)];
+                double flag = 0.0;
+                if (!finite(est) || !finite(hn)) flag = 1.0;
+                else if (est <= sp.tol * nb || !(hn > 1e-14 * diag)) flag = 2.0;   // converged or breakdown
+                ks.sc[2] = est / nb;
+                ks.sc[3] = flag;
             }
             __syncthreads();
-            const double est = fabs(ks.g[j + 1]);
-            const double diag = ks.H[j + j * (m + 1)];
             k = j + 1;
-            st.relres_est = est / nb;
-            if (!finite(est) || !finite(hn)) { st.status = FDE_ENONFINITE; break; }
-            const bool breakdown = !(hn > 1e-14 * diag);
-            if (est <= sp.tol * nb || breakdown) { converged = true; break; }
+            st.relres_est = ks.sc[2];
+            const double flag = ks.sc[3];
+            __syncthreads();   // ks.sc is rewritten by the next step's thread 0
+            if (flag == 1.0) { st.status = FDE_ENONFINITE; break; }
+            if (flag == 2.0) { converged = true; break; }
             if (st.iterations >= sp.max_iters) break;
         }
         if (st.status == FDE_ENONFINITE) break;
@@ -613,11 +627,16 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
             const W* b[1] = {q};
             if (!dots_pairs<W, 1>(t, N, a, b, ks)) return false;
         }
-        const double pq = ks.red[0];
-        if (!finite(pq)) { st.status = FDE_ENONFINITE; break; }
-        if (!(pq > 0.0)) { st.status = FDE_EBREAKDOWN; break; }
-        const double al = rz / pq;
-        const W alw = W(al);
+        // scalars by thread 0, broadcast through ks.sc (see gmres_right_core)
+        if (threadIdx.x == 0) {
+            const double pq = ks.red[0];
+            ks.sc[0] = !finite(pq) ? 1.0 : (!(pq > 0.0) ? 2.0 : 0.0);
+            ks.sc[1] = rz / pq;
+        }
+        __syncthreads();
+        if (ks.sc[0] == 1.0) { st.status = FDE_ENONFINITE; break; }
+        if (ks.sc[0] == 2.0) { st.status = FDE_EBREAKDOWN; break; }
+        const W alw = W(ks.sc[1]);
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             sol[i] = sol[i] + alw * ldw(p + i);
             r[i] = ldw(r + i) - alw * ldw(q + i);
@@ -627,20 +646,29 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
             const W* a[1] = {r};
             if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
         }
-        rr = ks.red[0];
-        st.relres_est = sqrt(rr) / nb;
-        if (!finite(rr)) { st.status = FDE_ENONFINITE; break; }
-        if (sqrt(rr) <= sp.tol * nb) { st.status = FDE_OK; break; }
+        if (threadIdx.x == 0) {
+            const double rrn = ks.red[0];
+            const double nr = sqrt(rrn);
+            ks.sc[2] = nr / nb;
+            ks.sc[3] = !finite(rrn) ? 1.0 : (nr <= sp.tol * nb ? 2.0 : 0.0);
+        }
+        __syncthreads();
+        st.relres_est = ks.sc[2];
+        if (ks.sc[3] == 1.0) { st.status = FDE_ENONFINITE; break; }
+        if (ks.sc[3] == 2.0) { st.status = FDE_OK; break; }
         if (!op_tau<W>(t, I, lm, r, W(1), z, wk)) return false;
         {
             const W* a[1] = {r};
             const W* b[1] = {z};
             if (!dots_pairs<W, 1>(t, N, a, b, ks)) return false;
         }
-        const double rz_new = ks.red[0];
-        const double be = rz_new / rz;
-        rz = rz_new;
-        const W bew = W(be);
+        if (threadIdx.x == 0) {
+            const double rz_new = ks.red[0];
+            ks.sc[4] = rz_new / rz;
+            rz = rz_new;
+        }
+        __syncthreads();
+        const W bew = W(ks.sc[4]);
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) p[i] = ldw(z + i) + bew * ldw(p + i);
         if (!team_sync(t)) return false;
     }

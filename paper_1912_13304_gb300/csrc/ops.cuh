@@ -291,13 +291,16 @@ FDE_NI void split_fwd_cols(const Team& t, const Inst& I, const Wk& wk, Combo<W> 
             buf[pad(c * P1 + m1)] = pack_elem<W, EXT>(get, P2 * m1 + m2b + c, n, Np);
         }
         __syncthreads();
+        trace_mark(t, 50);
         fft_lines<W, false>(buf, A.logP1, cc, P1, wk.tw);
+        trace_mark(t, 51);
         for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
             const int c = idx % cc, j1 = idx / cc;
             const int m2 = m2b + c;
             Y[(long long)j1 * P2 + m2] = buf[pad(c * P1 + j1)] * g[(j1 * m2) << tsh];
         }
         __syncthreads();
+        trace_mark(t, 52);
     }
 }
 
@@ -388,6 +391,7 @@ FDE_NI void split_inv_cols(const Team& t, const Inst& I, const Wk& wk, const cx<
     for (int un = t.rank; un < units; un += t.size) {
         const int m2b = un * cc;
         split_inv_unit_fft<W>(I, wk, Y, Y2, m2b, cc, two);
+        trace_mark(t, 57);
         const int total = (A.P1 / 2) * cc * 2;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int m1 = idx / (2 * cc);
@@ -425,6 +429,7 @@ FDE_NI void split_tau_inv_mv_fwd(const Team& t, const Inst& I, const Wk& wk, con
     for (int un = t.rank; un < units; un += t.size) {
         const int m2b = un * cc;
         split_inv_unit_fft<W>(I, wk, Yt, nullptr, m2b, cc, false);
+        trace_mark(t, 53);
         for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
             const int c = idx / P1, m1 = idx - c * P1;
             const long long m = (long long)P2 * m1 + m2b + c;
@@ -445,7 +450,9 @@ FDE_NI void split_tau_inv_mv_fwd(const Team& t, const Inst& I, const Wk& wk, con
             buf[pad(idx)] = mk(zr[0], zr[1]);
         }
         __syncthreads();
+        trace_mark(t, 54);
         fft_lines<W, false>(buf, A.logP1, cc, P1, wk.tw);
+        trace_mark(t, 55);
         for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
             const int c = idx % cc, j1 = idx / cc;
             const int m2 = m2b + c;

@@ -82,23 +82,25 @@ FDE_D R warp_sum(R v) {
     return v;
 }
 
-// Block-wide sums of K per-thread values (K <= 8 at a time), written to
-// out[0..K) in shared memory.  Deterministic: fixed shuffle tree, then a
-// fixed-order sum over warps.
+// Block-wide sums of K per-thread values (K <= blockDim/32), written to
+// out[0..K) in shared memory.  The values are transposed through `wide`
+// (K * blockDim doubles of shared memory) and warp k sums column k: lane l
+// adds entries l, l+32, ... in order, then a fixed shuffle tree.  Each sum
+// costs blockDim/32 + 5 warp-wide FP64 adds instead of 5 per warp, which
+// matters where every FP64 warp instruction occupies the SM's FP64 pipe for
+// many cycles.  Deterministic.
 template <int K>
-FDE_D void block_sum(const double (&v)[K], double* out, double* scratch /* [K*32] smem */) {
+FDE_D void block_sum(const double (&v)[K], double* out, double* wide) {
+    const int nt = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const double s = warp_sum(v[k]);
-        if (lane == 0) scratch[k * 32 + warp] = s;
-    }
+    for (int k = 0; k < K; ++k) wide[k * nt + threadIdx.x] = v[k];
     __syncthreads();
-    if (threadIdx.x < K) {
+    if (warp < K) {
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += scratch[threadIdx.x * 32 + w];
-        out[threadIdx.x] = s;
+        for (int i = lane; i < nt; i += 32) s += wide[warp * nt + i];
+        s = warp_sum(s);
+        if (lane == 0) out[warp] = s;
     }
     __syncthreads();
 }
@@ -126,15 +128,24 @@ FDE_D void dot2_acc(F2& a, float x, float y) {
     a.c += e;
 }
 
-// Block-wide sums of K compensated FP32 values: warp trees in pairs, then
-// FP64 across warps.  out[0..K) in shared memory.
+// Block-wide sums of K compensated FP32 values, transposed through `wide`
+// (K * blockDim float pairs) like block_sum; warp k accumulates column k with
+// TwoSum, then a shuffle tree of compensated adds.  out[0..K) in FP64.
 template <int K>
-FDE_D void block_sum_f2(const F2 (&v)[K], double* out, double* scratch /* [K*32] smem */) {
+FDE_D void block_sum_f2(const F2 (&v)[K], double* out, double* wide) {
+    float2* w2 = reinterpret_cast<float2*>(wide);
+    const int nt = blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        F2 a = v[k];
+    for (int k = 0; k < K; ++k) w2[k * nt + threadIdx.x] = make_float2(v[k].s, v[k].c);
+    __syncthreads();
+    if (warp < K) {
+        F2 a{0.0f, 0.0f};
+        for (int i = lane; i < nt; i += 32) {
+            const float2 e = w2[warp * nt + i];
+            two_sum_acc(a, e.x);
+            a.c += e.y;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float os = __shfl_xor_sync(0xffffffffu, a.s, o);
@@ -142,13 +153,7 @@ FDE_D void block_sum_f2(const F2 (&v)[K], double* out, double* scratch /* [K*32]
             two_sum_acc(a, os);
             a.c += oc;
         }
-        if (lane == 0) scratch[k * 32 + warp] = (double)a.s + (double)a.c;
-    }
-    __syncthreads();
-    if (threadIdx.x < K) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += scratch[threadIdx.x * 32 + w];
-        out[threadIdx.x] = s;
+        if (lane == 0) out[warp] = (double)a.s + (double)a.c;
     }
     __syncthreads();
 }
