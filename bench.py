@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--precisions", default="f64,f32_ir")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inner-tol", type=float, default=1e-3)
+    ap.add_argument("--graph", type=int, default=1, help="1: replay the time-step loop as a CUDA graph")
+    ap.add_argument("--balance", type=int, default=1,
+                    help="1: team sizes follow the previous time step's iteration counts")
     return ap.parse_args()
 
 
@@ -147,27 +150,12 @@ def run_ours(args, rank, world, device):
     fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
 
     results = {}
+    from paper_1912_13304_gb300.solver import TimeStepper
+
     for prec in [p for p in args.precisions.split(",") if p]:
         plans = [fde.Plan.from_workload(w, precision=prec, device=device) for w in ws]
         u = [torch.empty(n, dtype=torch.float64, device=device) for _ in ws]
-        b = [torch.empty_like(x) for x in u]
-        info = torch.zeros(TIME_STEPS * len(ws) * fde.INFO_BYTES, dtype=torch.uint8, device=device)
-        isz = len(ws) * fde.INFO_BYTES
-
-        def one_step(events=None, h2d=False):
-            if h2d:
-                for k in range(len(ws)):
-                    u[k].copy_(u0_host[k], non_blocking=True)
-            for m in range(TIME_STEPS):
-                for k, p in enumerate(plans):
-                    p.rhs(u[k], b=b[k])
-                if events is not None:
-                    events[m][0].record()
-                fde.solve_batch(plans, b, u, tol=TOL, max_iters=20000, inner_tol=args.inner_tol,
-                                max_outer=200, info_dev=info[m * isz:(m + 1) * isz], read_info=False)
-                if events is not None:
-                    events[m][1].record()
-
+        kw = dict(tol=TOL, max_iters=20000, inner_tol=args.inner_tol, max_outer=200, balance=bool(args.balance))
         u0_dev = [x.to(device) for x in u0_host]
 
         def reset():
@@ -175,31 +163,45 @@ def run_ours(args, rank, world, device):
                 u[k].copy_(u0_dev[k])
             flush.fill_(1.0)
 
+        # eager warm-up (also the launch-duration pass below), then the loop of
+        # TIME_STEPS steps captured once as a CUDA graph
+        eager = TimeStepper(plans, u, TIME_STEPS, graph=False, **kw)
         for _ in range(args.warmup):
             reset()
-            one_step()
+            eager.run()
         torch.cuda.synchronize()
-        # timed region: K steps, L2 flushed before each, device events
-        step_ms, launch_ms = [], []
+        stepper = TimeStepper(plans, u, TIME_STEPS, graph=bool(args.graph), **kw)
+        for _ in range(args.warmup):
+            reset()
+            stepper.run()
+        torch.cuda.synchronize()
+        # timed region: K bench steps (graph replays), L2 flushed before each, device events
+        step_ms = []
         with ClockSampler(torch.cuda.current_device()) as clk:
             for _ in range(args.steps):
                 reset()
-                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                      for _ in range(TIME_STEPS)]
                 s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 if world > 1:
                     torch.distributed.barrier()
                 torch.cuda.synchronize()
                 s0.record()
-                one_step(ev)
+                stepper.run()
                 s1.record()
                 torch.cuda.synchronize()
                 step_ms.append(s0.elapsed_time(s1))
-                launch_ms += [a.elapsed_time(c) for a, c in ev]
-        infos = fde.decode_info(info.cpu().numpy().tobytes(), TIME_STEPS * len(ws))
+        infos = [i for step in stepper.infos() for i in step]
         its = sum(i["iterations"] for i in infos)
         worst = max(i["relres"] for i in infos)
         ok = all(i["status"] == fde.OK and i["relres"] <= TOL for i in infos)
+        # duration of each solve launch: the same steps as eager launches with events around each
+        launch_ms = []
+        for _ in range(args.steps):
+            reset()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(TIME_STEPS)]
+            eager.run_eager(ev)
+            torch.cuda.synchronize()
+            launch_ms += [a.elapsed_time(c) for a, c in ev]
         # end to end: inputs from pinned host memory, solution back to host, every step
         e2e_ms = []
         out_host = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in ws]
@@ -208,7 +210,9 @@ def run_ours(args, rank, world, device):
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             s0.record()
-            one_step(h2d=True)
+            for k in range(len(ws)):
+                u[k].copy_(u0_host[k], non_blocking=True)
+            stepper.run()
             for k in range(len(ws)):
                 out_host[k].copy_(u[k], non_blocking=True)
             s1.record()
@@ -328,13 +332,17 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"1d-var-n{n}-3alpha-20steps-gmres30", "n": n, "alphas": list(ALPHAS),
                        "time_steps": TIME_STEPS, "restart": RESTART, "tol": TOL, "precision": head_k,
-                       "batched": "3 alphas per launch", "l2": "flushed (512 MB write) before each step"},
+                       "batched": "3 alphas per launch", "l2": "flushed (512 MB write) before each step",
+                       "teams": "sized by the previous time step's iteration counts" if args.balance
+                       else "even split",
+                       "launch": "20 time steps replayed as one CUDA graph" if args.graph else "eager"},
             "unknown_iters_per_s": head["unknown_iters_per_s"] * world,
             "iterations_per_step": head["iterations"],
             "worst_relres": head["worst_relres"],
             "e2e": {"value": nsolves / (head["e2e_ms"] * 1e-3), "unit": "solves/s",
                     "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step},
-            "gpu_launches": (TIME_STEPS * (len(ALPHAS) + 1)) * args.steps,
+            # per time step: one fde_step_rhs per alpha, k_balance when balancing, the engine
+            "gpu_launches": (TIME_STEPS * (len(ALPHAS) + 1 + (1 if args.balance else 0))) * args.steps,
             "roofline": head["roofline"], "clocks": head["clocks"],
             "paths": {k: {kk: v[kk] for kk in ("ms_per_step", "solves_per_s", "unknown_iters_per_s", "iterations",
                                                 "outer", "worst_relres", "converged", "roofline", "launch_ms")}

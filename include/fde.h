@@ -94,6 +94,12 @@ typedef struct {
     double inner_tol;      /* FDE_PREC_F32_IR: relative tolerance of each inner solve */
     int max_outer;         /* FDE_PREC_F32_IR: cap on refinement steps */
     int side;              /* fde_side (GMRES only; PCG ignores it) */
+    int balance;           /* fde_krylov_solve with count > 1: 0 splits the GPU evenly over the
+                              instances; 1 sizes each instance's team in proportion to
+                              N log2(L) times the iteration count that info_dev[i] holds from
+                              the previous solve of the same plans, in the same order (zeros:
+                              even split).  Time stepping keeps the counts stable from step
+                              to step. */
 } fde_solve_opts;
 
 /* Per-solve result, written by the device into caller memory. */

@@ -46,7 +46,7 @@ class FdeSolveOpts(ctypes.Structure):
     _fields_ = [
         ("method", ctypes.c_int), ("restart", ctypes.c_int), ("tol", ctypes.c_double),
         ("max_iters", ctypes.c_int), ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double),
-        ("max_outer", ctypes.c_int), ("side", ctypes.c_int),
+        ("max_outer", ctypes.c_int), ("side", ctypes.c_int), ("balance", ctypes.c_int),
     ]
 
 
@@ -143,7 +143,7 @@ def default_opts() -> FdeSolveOpts:
 
 
 def make_opts(method="gmres", restart=30, tol=1e-8, max_iters=5000, precision="f64", inner_tol=1e-4,
-              max_outer=50, side="right") -> FdeSolveOpts:
+              max_outer=50, side="right", balance=False) -> FdeSolveOpts:
     o = FdeSolveOpts()
     o.method = {"pcg": PCG, "gmres": GMRES}[method] if isinstance(method, str) else method
     o.restart = restart
@@ -154,6 +154,7 @@ def make_opts(method="gmres", restart=30, tol=1e-8, max_iters=5000, precision="f
     o.inner_tol = inner_tol
     o.max_outer = max_outer
     o.side = {"right": SIDE_RIGHT, "left": SIDE_LEFT}[side] if isinstance(side, str) else side
+    o.balance = int(bool(balance))
     return o
 
 

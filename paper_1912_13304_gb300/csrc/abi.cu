@@ -313,6 +313,54 @@ __global__ void k_step_rhs(long long N, double c0, double ha, const double* u, c
         b[i] = c0 * u[i] + (f ? ha * f[i] : 0.0);
 }
 
+// Team sizes for one batched solve: instance i gets a share of the G CTAs in
+// proportion to cost[i] times the iteration count its previous solve left in
+// info[i] (at least one CTA each).  One thread; writes team_start[0..count].
+struct BalanceJob {
+    int count, G;
+    const fde_solve_info* info;
+    SyncArea* sync;
+    float cost[kMaxBatch];
+};
+
+__global__ void k_balance(const __grid_constant__ BalanceJob J) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double w[kMaxBatch];
+    int ts[kMaxBatch];
+    double W = 0.0;
+    for (int i = 0; i < J.count; ++i) {
+        int it = J.info[i].iterations;
+        if (it < 1 || it > 1000000) it = 1;
+        w[i] = (double)J.cost[i] * (double)it;
+        W += w[i];
+    }
+    int used = 0;
+    for (int i = 0; i < J.count; ++i) {
+        int v = (int)((double)J.G * w[i] / W);
+        ts[i] = v < 1 ? 1 : v;
+        used += ts[i];
+    }
+    while (used > J.G) {                  // the one-CTA floor overshot: shrink the largest
+        int b = 0;
+        for (int i = 1; i < J.count; ++i) if (ts[i] > ts[b]) b = i;
+        if (ts[b] <= 1) break;
+        --ts[b];
+        --used;
+    }
+    while (used < J.G) {                  // spare CTAs to the most loaded team per CTA
+        int b = 0;
+        for (int i = 1; i < J.count; ++i) if (w[i] * ts[b] > w[b] * ts[i]) b = i;
+        ++ts[b];
+        ++used;
+    }
+    int acc = 0;
+    for (int i = 0; i < J.count; ++i) {
+        J.sync->team_start[i] = (unsigned short)acc;
+        acc += ts[i];
+    }
+    J.sync->team_start[J.count] = (unsigned short)acc;
+}
+
 template <typename T>
 T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + off); }
 
@@ -363,6 +411,7 @@ void fde_default_opts(fde_solve_opts* o) {
     o->inner_tol = 1e-4;
     o->max_outer = 50;
     o->side = FDE_SIDE_RIGHT;
+    o->balance = 0;
 }
 
 const char* fde_status_string(int s) {
@@ -606,6 +655,7 @@ fde_status fde_krylov_solve(const fde_plan* const* plans, int count, const doubl
     if (!(opts->tol > 0.0) || opts->max_iters < 1 || (opts->side != FDE_SIDE_RIGHT && opts->side != FDE_SIDE_LEFT))
         return FDE_EINVAL;
     if (p0->opts.precision == FDE_PREC_F32_IR && (!(opts->inner_tol > 0.0) || opts->max_outer < 1)) return FDE_EINVAL;
+    if (opts->balance != 0 && opts->balance != 1) return FDE_EINVAL;
     const int mode = p0->opts.precision;
     EngineArgs* a = new (std::nothrow) EngineArgs();
     if (!a) return FDE_ENOMEM;
@@ -646,8 +696,32 @@ fde_status fde_krylov_solve(const fde_plan* const* plans, int count, const doubl
         grid = ts * count;
     }
     a->team_size = ts;
+    a->team_mode = 0;
+    const bool balanced = opts->balance == 1 && !all_cta && count > 1 && count < G;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(p0->sync_dev, 0, offsetof(SyncArea, partial), st);
+    if (e == cudaSuccess && balanced) {
+        BalanceJob* B = new (std::nothrow) BalanceJob();
+        if (!B) {
+            delete a;
+            return FDE_ENOMEM;
+        }
+        B->count = count;
+        B->G = G;
+        B->info = info_dev;
+        B->sync = p0->sync_dev;
+        for (int i = 0; i < count; ++i) {
+            const Inst& I = plans[i]->inst;
+            double c = 0.0;
+            for (int ax = 0; ax < I.dim; ++ax) c += (double)I.N * (I.ax[ax].logNp + 1);
+            B->cost[i] = (float)c;
+        }
+        k_balance<<<1, 32, 0, st>>>(*B);
+        delete B;
+        e = cudaGetLastError();
+        a->team_mode = 1;
+        grid = G;
+    }
     if (e == cudaSuccess) {
         if (mode == FDE_PREC_F64) e = engine_launch_f64(*a, grid, st);
         else if (mode == FDE_PREC_F32) e = engine_launch_f32(*a, grid, st);

@@ -95,6 +95,7 @@ struct SyncArea {
     unsigned int abort_flag;
     unsigned int trace_n;              // FDE_TRACE builds: entries written to trace[]
     unsigned int pad[61];
+    unsigned short team_start[kMaxBatch + 2];  // variable teams: team i = CTAs [start[i], start[i+1])
     double partial[kMaxCtas * kMaxDots];
     unsigned long long trace[kTraceEntries];   // (code << 48) | globaltimer ns
 };

@@ -14,7 +14,8 @@ enum Mode : int { kModeF64 = 0, kModeF32 = 1, kModeIR = 2 };
 struct EngineArgs {
     int op;
     int count;
-    int team_size;
+    int team_size;             // team_mode 0: every team has team_size CTAs
+    int team_mode;             // 1: team i = CTAs [sync->team_start[i], team_start[i+1]), instance i
     int dtype;                 // operator calls: FDE_F64 / FDE_F32
     int smem_bytes;            // dynamic shared memory of the launch
     SyncArea* sync;
@@ -146,16 +147,30 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
     extern __shared__ __align__(256) unsigned char dsm[];
     __shared__ Inst s_inst;
     __shared__ unsigned int s_next;
-    const int ts = a.team_size;
-    const int nteams = gridDim.x / ts;
-    const int team_id = blockIdx.x / ts;
-    if (team_id >= nteams) return;
+    int ts, nteams, team_id, first;
+    if (a.team_mode == 1) {
+        // sizes written by k_balance earlier on the stream
+        const unsigned short* st = a.sync->team_start;
+        nteams = a.count;
+        team_id = -1;
+        for (int i = 0; i < nteams; ++i)
+            if ((int)blockIdx.x >= st[i] && (int)blockIdx.x < st[i + 1]) { team_id = i; break; }
+        if (team_id < 0) return;
+        first = st[team_id];
+        ts = st[team_id + 1] - first;
+    } else {
+        ts = a.team_size;
+        nteams = gridDim.x / ts;
+        team_id = blockIdx.x / ts;
+        if (team_id >= nteams) return;
+        first = team_id * ts;
+    }
     Team t;
-    t.rank = blockIdx.x - team_id * ts;
+    t.rank = blockIdx.x - first;
     t.size = ts;
     t.count = &a.sync->bar_count[team_id];
     t.gen = &a.sync->bar_gen[team_id];
-    t.partial = a.sync->partial + (size_t)team_id * ts * kMaxDots;
+    t.partial = a.sync->partial + (size_t)first * kMaxDots;
     t.abort_flag = &a.sync->abort_flag;
     t.sync = a.sync;
     int next_static = team_id;
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
         }
         if (idx >= a.count) break;
         if (*reinterpret_cast<volatile unsigned int*>(&a.sync->abort_flag)) break;
-        const int inst_i = a.order[idx];
+        const int inst_i = a.team_mode == 1 ? idx : a.order[idx];
         {
             const int* src = reinterpret_cast<const int*>(a.inst[inst_i]);
             int* dst = reinterpret_cast<int*>(&s_inst);

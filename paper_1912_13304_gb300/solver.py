@@ -115,12 +115,15 @@ class Plan:
 
 def solve_batch(plans: Sequence[Plan], b: Sequence, x: Sequence, tol: float = 1e-8, max_iters: int = 5000,
                 inner_tol: float = 1e-4, max_outer: int = 50, side: str = "right", info_dev=None, stream=None,
-                read_info: bool = True):
-    """One fde_krylov_solve launch over several plans (same method/precision/restart)."""
+                read_info: bool = True, balance: bool = False):
+    """One fde_krylov_solve launch over several plans (same method/precision/restart).
+    With ``balance``, ``info_dev`` must hold the previous solve's results for
+    the same plans (or zeros): team sizes follow its iteration counts."""
     torch = _torch()
     p0 = plans[0]
     opts = make_opts(method=p0.opts.method, restart=p0.opts.restart, tol=tol, max_iters=max_iters,
-                     precision=p0.opts.precision, inner_tol=inner_tol, max_outer=max_outer, side=side)
+                     precision=p0.opts.precision, inner_tol=inner_tol, max_outer=max_outer, side=side,
+                     balance=balance)
     if info_dev is None:
         info_dev = torch.zeros(len(plans) * INFO_BYTES, dtype=torch.uint8, device=p0.device)
     krylov_solve([p.handle for p in plans], b, x, opts, info_dev, stream)
@@ -128,3 +131,66 @@ def solve_batch(plans: Sequence[Plan], b: Sequence, x: Sequence, tol: float = 1e
         return info_dev
     raw = info_dev.cpu().numpy().tobytes()
     return decode_info(raw, len(plans))
+
+
+class TimeStepper:
+    """Implicit-Euler time stepping of several plans together (Sec. 1.2: each
+    step solves M u_m = c0 u_{m-1} + h^alpha f with x0 = u_{m-1}): per step one
+    fde_step_rhs per plan and one batched fde_krylov_solve.  With ``graph``
+    the whole loop of ``steps`` steps is captured once in a CUDA graph and
+    ``run()`` replays it; ``u`` (device tensors, updated in place) and the
+    per-step info buffer are the graph's fixed inputs and outputs.  With
+    ``balance`` each step sizes the instances' teams from the previous step's
+    iteration counts (the first step splits evenly)."""
+
+    def __init__(self, plans: Sequence[Plan], u: Sequence, steps: int, *, tol: float = 1e-8,
+                 max_iters: int = 5000, inner_tol: float = 1e-4, max_outer: int = 50, balance: bool = True,
+                 graph: bool = True):
+        torch = _torch()
+        self.plans = list(plans)
+        self.u = list(u)
+        self.steps = steps
+        self.b = [torch.empty_like(x) for x in self.u]
+        self.isz = len(self.plans) * INFO_BYTES
+        self.info = torch.zeros(steps * self.isz, dtype=torch.uint8, device=self.u[0].device)
+        self.kw = dict(tol=tol, max_iters=max_iters, inner_tol=inner_tol, max_outer=max_outer, balance=balance)
+        self.graph = None
+        if graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._loop()
+            self.graph = g
+
+    def _loop(self, events=None):
+        for m in range(self.steps):
+            for k, p in enumerate(self.plans):
+                p.rhs(self.u[k], b=self.b[k])
+            cur = self.info[m * self.isz:(m + 1) * self.isz]
+            if self.kw["balance"]:
+                if m == 0:
+                    cur.zero_()
+                else:
+                    cur.copy_(self.info[(m - 1) * self.isz:m * self.isz])
+            if events is not None:
+                events[m][0].record()
+            solve_batch(self.plans, self.b, self.u, info_dev=cur, read_info=False, **self.kw)
+            if events is not None:
+                events[m][1].record()
+
+    def run_eager(self, events=None):
+        """All steps as eager launches; events[m] = (start, end) CUDA events
+        recorded around step m's solve launch."""
+        self._loop(events)
+
+    def run(self):
+        """All steps on the current stream (graph replay or eager launches)."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._loop()
+
+    def infos(self) -> list[list[dict]]:
+        """Per step, per plan: the decoded fde_solve_info."""
+        flat = decode_info(self.info.cpu().numpy().tobytes(), self.steps * len(self.plans))
+        n = len(self.plans)
+        return [flat[m * n:(m + 1) * n] for m in range(self.steps)]
