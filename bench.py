@@ -34,6 +34,9 @@ TIME_STEPS = 20
 RESTART = 30
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+# dram__bytes_read.sum + dram__bytes_write.sum of one FP64 engine launch of this
+# workload (balanced teams), from the ncu capture summarised under profiles/
+F64_LAUNCH_DRAM_BYTES = 252.841472e6 + 555.247616e6
 
 
 def parse():
@@ -47,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--graph", type=int, default=1, help="1: replay the time-step loop as a CUDA graph")
+    ap.add_argument("--batch", type=int, default=1, help="1: also time the 256-instance batched workload")
     ap.add_argument("--balance", type=int, default=1,
                     help="1: team sizes follow the previous time step's iteration counts")
     return ap.parse_args()
@@ -224,8 +228,9 @@ def run_ours(args, rank, world, device):
         avg_launch = sum(launch_ms) / len(launch_ms)
         if prec == "f64":
             achieved = per_launch_its * fpi / (avg_launch * 1e-3) / 1e12
+            # DRAM read + write of one balanced FP64 launch (ncu; profiles/fde_engine_f64_n65535_3alpha.md)
             roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak_tflops, "traffic": None,
+                    "frac": achieved / fp64_peak_tflops, "traffic": F64_LAUNCH_DRAM_BYTES if args.balance else None,
                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz"}
         else:
             achieved = per_launch_its * bpi / (avg_launch * 1e-3) / 1e9
@@ -242,6 +247,63 @@ def run_ours(args, rank, world, device):
         for p in plans:
             p.close()
     return results
+
+
+def run_batch(args, device):
+    """The batched workload: 256 independent 1D constant-coefficient solves
+    (n = 2^k - 1, k ~ U{8..14}; alpha ~ U(1.1, 1.9); d, dt per instance; seed
+    2), PCG with each instance's shifted tau preconditioner, relres 1e-8, all
+    in one persistent launch (one-CTA teams taking instances from a queue,
+    largest first).  Reported per precision path: solves/s and
+    unknown-iterations/s."""
+    import torch
+
+    import paper_1912_13304_gb300 as fde
+    import workloads
+    ws = workloads.config4()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    out = {}
+    for prec in [p for p in args.precisions.split(",") if p]:
+        plans = [fde.Plan.from_workload(w, precision=prec, device=device) for w in ws]
+        bs = [p.c0 * torch.tensor(w["b"], dtype=torch.float64, device=device) for p, w in zip(plans, ws)]
+        xs = [torch.zeros_like(b) for b in bs]
+        info = torch.zeros(len(ws) * fde.INFO_BYTES, dtype=torch.uint8, device=device)
+
+        def once():
+            for x in xs:
+                x.zero_()
+            fde.solve_batch(plans, bs, xs, tol=TOL, max_iters=2000, inner_tol=1e-4, max_outer=100,
+                            info_dev=info, read_info=False)
+
+        for _ in range(args.warmup):
+            once()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            for x in xs:
+                x.zero_()
+            flush.fill_(1.0)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            s0.record()
+            fde.solve_batch(plans, bs, xs, tol=TOL, max_iters=2000, inner_tol=1e-4, max_outer=100,
+                            info_dev=info, read_info=False)
+            s1.record()
+            torch.cuda.synchronize()
+            ms.append(s0.elapsed_time(s1))
+        infos = fde.decode_info(info.cpu().numpy().tobytes(), len(ws))
+        t = sum(ms) / len(ms)
+        unk = sum(w["n1"] * i["iterations"] for w, i in zip(ws, infos))
+        out[prec] = {"ms_per_launch": t, "solves_per_s": len(ws) / (t * 1e-3),
+                     "unknown_iters_per_s": unk / (t * 1e-3),
+                     "iterations": sum(i["iterations"] for i in infos),
+                     "outer": sum(i["outer"] for i in infos),
+                     "worst_relres": max(i["relres"] for i in infos),
+                     "converged": all(i["status"] == fde.OK and i["relres"] <= TOL for i in infos)}
+        for p in plans:
+            p.close()
+    return {"workload": "batch256-1d-const-n255..16383-pcg-shifted-tau", "instances": len(ws),
+            "unknowns": sum(w["n1"] for w in ws), "paths": out}
 
 
 def cpu_baseline_sample(n: int):
@@ -311,6 +373,7 @@ def main():
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     res = run_ours(args, rank, world, device)
+    batch = run_batch(args, device) if args.batch else None
     # headline: the fastest precision path that met relres 1e-8 on every solve
     good = {k: v for k, v in res.items() if v["converged"]}
     head_k = max(good or res, key=lambda k: (good or res)[k]["solves_per_s"])
@@ -348,6 +411,8 @@ def main():
                                                 "outer", "worst_relres", "converged", "roofline", "launch_ms")}
                       for k, v in res.items()},
         }
+        if batch is not None:
+            line["batched_workload"] = batch
         if world == 1 and not args.no_cpu_baseline:
             try:
                 line["cpu_baseline"] = cpu_baseline_sample(n)

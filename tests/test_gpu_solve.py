@@ -297,3 +297,28 @@ def test_graph_time_stepping_replays_the_eager_steps(gpu):
     for step in graph.infos():
         for inf in step:
             assert inf["status"] == fde.OK and inf["relres"] <= 1e-8, inf
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32_ir"])
+def test_batched_256_instances_full_size(gpu, precision):
+    # The full batched workload (n up to 16383, so one-CTA teams also run the
+    # split-line layout): every instance converges, and a sample spanning the
+    # sizes matches the oracle's PCG iteration counts and residuals.
+    ws = workloads.config4()
+    plans = [fde.Plan.from_workload(w, precision=precision) for w in ws]
+    bs = [to_dev(gpu, p.c0 * w["b"], "f64") for p, w in zip(plans, ws)]
+    xs = [gpu.zeros_like(b) for b in bs]
+    infos = fde.solve_batch(plans, bs, xs, tol=1e-8, max_iters=2000, inner_tol=1e-4, max_outer=100)
+    for inf in infos:
+        assert inf["status"] == fde.OK and inf["relres"] <= 1e-8, inf
+    sizes = sorted(range(len(ws)), key=lambda i: ws[i]["n1"])
+    sample = sorted(set(sizes[::40] + [sizes[-1], sizes[-2]]))
+    for i in sample:
+        w = ws[i]
+        prob = oracle_problem_1d(w)
+        b = prob.c0 * w["b"]
+        ref = oracle.pcg(prob.matvec, b, Pinv=oracle.Tau1D.for_problem(prob, shift=True).apply_inverse, tol=1e-8)
+        if precision == "f64":
+            assert abs(infos[i]["iterations"] - ref.iterations) <= 1, (w["n1"], infos[i], ref.iterations)
+        x = xs[i].cpu().numpy()
+        assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8, (w["n1"], infos[i])
