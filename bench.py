@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=1e-3)
     ap.add_argument("--graph", type=int, default=1, help="1: replay the time-step loop as a CUDA graph")
     ap.add_argument("--batch", type=int, default=1, help="1: also time the 256-instance batched workload")
+    ap.add_argument("--two-d", type=int, default=1, help="1: also time the two 2D workloads")
     ap.add_argument("--balance", type=int, default=1,
                     help="1: team sizes follow the previous time step's iteration counts")
     return ap.parse_args()
@@ -306,6 +307,79 @@ def run_batch(args, device):
             "unknowns": sum(w["n1"] for w in ws), "paths": out}
 
 
+# Algorithmic vector passes per iteration of the 2D solves (each pass reads or
+# writes N elements once): PCG with P_hat about 11, GMRES(20) with D_N about 34.
+PASSES_2D = {"pcg": 11, "gmres": 34}
+
+
+def run_2d(args, device):
+    """The two 2D workloads, one solve each per bench step: 2047^2 constant
+    coefficients (alpha 1.5, beta 1.7, PCG with P_hat, seed 1) and 4095^2
+    variable coefficients (alpha 1.3, beta 1.8, one implicit-Euler step from
+    u0 = sin(pi x) sin(pi y), GMRES(20) with the 2D tau(F) D_N).  Reported per
+    precision path: solves/s, unknown-iterations/s and the algorithmic HBM
+    bandwidth (vector passes x element bytes x N per iteration) against the
+    measured copy peak."""
+    import torch
+
+    import paper_1912_13304_gb300 as fde
+    import workloads
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    out = {}
+    for name, w in (("2d-const-n2047-pcg-phat", workloads.config3()),
+                    ("2d-var-n4095-gmres20-one-step", workloads.config5(steps=1))):
+        res = {}
+        N = w["n1"] * w["n2"]
+        for prec in [p for p in args.precisions.split(",") if p]:
+            plan = fde.Plan.from_workload(w, precision=prec, device=device)
+            if w["rhs_scale"] == "unit":
+                b = plan.c0 * torch.tensor(w["b"], dtype=torch.float64, device=device)
+                x0 = torch.zeros_like(b)
+            else:
+                x0 = torch.tensor(w["u0"], dtype=torch.float64, device=device)
+                b = plan.rhs(x0)
+            x = torch.empty_like(b)
+            info = torch.zeros(fde.INFO_BYTES, dtype=torch.uint8, device=device)
+            kw = dict(tol=TOL, max_iters=5000, inner_tol=1e-4, max_outer=100, info_dev=info, read_info=False)
+            for _ in range(args.warmup):
+                x.copy_(x0)
+                fde.solve_batch([plan], [b], [x], **kw)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                x.copy_(x0)
+                flush.fill_(1.0)
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                s0.record()
+                fde.solve_batch([plan], [b], [x], **kw)
+                s1.record()
+                torch.cuda.synchronize()
+                ms.append(s0.elapsed_time(s1))
+            inf = fde.decode_info(info.cpu().numpy().tobytes(), 1)[0]
+            t = sum(ms) / len(ms)
+            elem = 8 if prec == "f64" else 4
+            gbs = inf["iterations"] * PASSES_2D[w["method"]] * elem * N / (t * 1e-3) / 1e9
+            res[prec] = {"ms_per_solve": t, "solves_per_s": 1e3 / t,
+                         "unknown_iters_per_s": N * inf["iterations"] / (t * 1e-3),
+                         "iterations": inf["iterations"], "outer": inf["outer"], "relres": inf["relres"],
+                         "converged": inf["status"] == fde.OK and inf["relres"] <= TOL,
+                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                      "frac": gbs / hbm_peak, "traffic": None}}
+            plan.close()
+            del x, b, x0
+            torch.cuda.empty_cache()
+        out[name] = {"unknowns": N, "paths": res}
+    return out
+
+
 def cpu_baseline_sample(n: int):
     """The oracle as it stands on a bounded sample of the workload: the
     first implicit-Euler solve of the alpha = 1.8 line, n = 65535, with the
@@ -374,6 +448,7 @@ def main():
     device = torch.device("cuda", local)
     res = run_ours(args, rank, world, device)
     batch = run_batch(args, device) if args.batch else None
+    two_d = run_2d(args, device) if args.two_d else None
     # headline: the fastest precision path that met relres 1e-8 on every solve
     good = {k: v for k, v in res.items() if v["converged"]}
     head_k = max(good or res, key=lambda k: (good or res)[k]["solves_per_s"])
@@ -413,6 +488,8 @@ def main():
         }
         if batch is not None:
             line["batched_workload"] = batch
+        if two_d is not None:
+            line["workloads_2d"] = two_d
         if world == 1 and not args.no_cpu_baseline:
             try:
                 line["cpu_baseline"] = cpu_baseline_sample(n)

@@ -386,7 +386,8 @@ int line_modes(const fde_problem* p, const Layout& Lo, int work_bytes) {
     const int nbuf = sym ? 1 : 2;
     // a whole line in one CTA: one FFT item per thread and the buffers in shared memory
     auto fits = [&](int esz) {
-        return fft_items_per_line(ilog2(Np)) <= kThreads && (long long)padded_len(Np * nbuf) * esz <= work_bytes;
+        return fft_lines_per_call(ilog2(Np), kThreads, esz / 2) >= 1 &&
+               (long long)padded_len(Np * nbuf) * esz <= work_bytes;
     };
     const int m64 = fits((int)sizeof(cx<double>)) ? kLineCta : kLineSplit;
     const int m32 = fits((int)sizeof(cx<float>)) ? kLineCta : kLineSplit;

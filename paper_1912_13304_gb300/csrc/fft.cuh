@@ -180,19 +180,26 @@ FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, 
 
 // In-place FFT of nlines lines held in (padded) shared memory, every pass
 // one radix item per thread (registers hold RAD values), so a call requires
-// nlines * P / RAD <= blockDim.x for the smallest radix it uses.
+// nlines * P / RAD <= kFftItems<R> * blockDim.x for the smallest radix it uses.
+//
+// Radix items per thread and pass: two for FP32 (twice the butterflies
+// between two barriers, registers to spare), one for FP64 (whose 8-point
+// butterfly already holds 32 registers).
+template <typename R> constexpr int kFftItems = sizeof(R) == 4 ? 2 : 1;
+
 template <typename R, bool INV>
 FDE_D void fft_inplace(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
+    constexpr int K = kFftItems<R>;
     const bool smem_tw = logP <= tw.logT;
     int logNs = 0;
     int rem = logP;
     while (rem >= 3) {
-        stockham_pass_inplace<R, 8, 8, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        stockham_pass_inplace<R, 8, 8 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
         logNs += 3;
         rem -= 3;
     }
-    if (rem == 2) stockham_pass_inplace<R, 4, 4, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
-    else if (rem == 1) stockham_pass_inplace<R, 2, 2, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+    if (rem == 2) stockham_pass_inplace<R, 4, 4 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+    else if (rem == 1) stockham_pass_inplace<R, 2, 2 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
 }
 
 // Radix items per line of the widest pass (the last one, whose radix is the
@@ -202,16 +209,19 @@ FDE_HD int fft_items_per_line(int logP) {
     const int last = r == 0 ? 3 : r;
     return logP >= last ? 1 << (logP - last) : 1;
 }
-FDE_HD int fft_lines_per_call(int logP, int threads) { return threads / fft_items_per_line(logP); }
+FDE_HD int fft_lines_per_call(int logP, int threads, int elem_bytes) {
+    return threads * (elem_bytes == 4 ? 2 : 1) / fft_items_per_line(logP);
+}
 
 // FFT of nlines lines of 2^logP at stride lstride (flat index), in batches
 // of lines; the flat origin of a batch starting at line l0 is pad(l0 *
 // lstride), which commutes with pad() because lstride is a multiple of 16
-// whenever more than one batch is needed.  A single line longer than the CTA
-// covers one item per thread is not supported (callers split such lines).
+// whenever more than one batch is needed.  A single line with more radix
+// items than kFftItems<R> per thread is not supported (callers split such
+// lines).
 template <typename R, bool INV>
 FDE_D void fft_lines(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
-    const int cap = fft_lines_per_call(logP, blockDim.x);
+    const int cap = fft_lines_per_call(logP, blockDim.x, (int)sizeof(R));
     for (int l0 = 0; l0 < nlines; l0 += cap) {
         const int nl = (nlines - l0) < cap ? (nlines - l0) : cap;
         fft_inplace<R, INV>(buf + pad(l0 * lstride), logP, nl, lstride, tw);

@@ -146,14 +146,99 @@ FDE_D bool dots_own(const Team& t, long long N, const W* a, const W* V, const do
     return team_allreduce(t, ks.red, tot);
 }
 
+// The same over the team's contiguous ranges: each thread keeps two elements'
+// loads of 8 vectors in flight.
 template <typename W>
 FDE_D bool dots_basis(const Team& t, long long N, const W* a, const W* V, const double* vs, int cnt, bool norm,
                       KShared& ks) {
     long long lo, hi;
     team_range(t, N, lo, hi);
-    return dots_own<W>(t, N, a, V, vs, cnt, norm, ks, [&](auto f) {
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) f(i);
-    });
+    const int tot = cnt + (norm ? 1 : 0);
+    const int nt = blockDim.x;
+    for (int c0 = 0; c0 < tot; c0 += 8) {
+        if constexpr (sizeof(W) == 8) {
+            double acc[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+            for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += 2 * nt) {
+                const long long i1 = i0 + nt;
+                const bool h1 = i1 < hi;
+                const double a0 = ldw(a + i0), a1 = h1 ? (double)ldw(a + i1) : 0.0;
+                double v0[8], v1[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int kk = c0 + k;
+                    v0[k] = kk < cnt ? (double)ldw(V + (long long)kk * N + i0) : a0;
+                    v1[k] = kk < cnt ? (h1 ? (double)ldw(V + (long long)kk * N + i1) : 0.0) : a1;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (c0 + k < tot) acc[k] += a0 * v0[k] + a1 * v1[k];
+            }
+            block_sum<8>(acc, ks.red + c0, ks.wide);
+        } else {
+            F2 acc[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = F2{0.0f, 0.0f};
+            for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += 2 * nt) {
+                const long long i1 = i0 + nt;
+                const bool h1 = i1 < hi;
+                const float a0 = (float)ldw(a + i0), a1 = h1 ? (float)ldw(a + i1) : 0.0f;
+                float v0[8], v1[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int kk = c0 + k;
+                    v0[k] = kk < cnt ? (float)ldw(V + (long long)kk * N + i0) : a0;
+                    v1[k] = kk < cnt ? (h1 ? (float)ldw(V + (long long)kk * N + i1) : 0.0f) : a1;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (c0 + k < tot) {
+                        dot2_acc(acc[k], a0, v0[k]);
+                        dot2_acc(acc[k], a1, v1[k]);
+                    }
+            }
+            block_sum_f2<8>(acc, ks.red + c0, ks.wide);
+        }
+    }
+    if (threadIdx.x < cnt) ks.red[threadIdx.x] *= vs[threadIdx.x];
+    __syncthreads();
+    trace_mark(t, 60);
+    return team_allreduce(t, ks.red, tot);
+}
+
+// V_j = w - sum_{q < cnt} c_q V_q over this CTA's contiguous part of the team
+// range, two elements and four vectors of loads in flight per thread.
+template <typename W>
+FDE_D void form_basis(const Team& t, long long N, const W* w, const W* V, const W* c, int cnt, W* out) {
+    long long lo, hi;
+    team_range(t, N, lo, hi);
+    const int nt = blockDim.x;
+    for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += 2 * nt) {
+        const long long i1 = i0 + nt;
+        const bool h1 = i1 < hi;
+        W a0 = ldw(w + i0), a1 = h1 ? ldw(w + i1) : W(0);
+        int q = 0;
+        for (; q + 4 <= cnt; q += 4) {
+            W v0[4], v1[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                v0[r] = ldw(V + (long long)(q + r) * N + i0);
+                v1[r] = h1 ? ldw(V + (long long)(q + r) * N + i1) : W(0);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                a0 -= c[q + r] * v0[r];
+                a1 -= c[q + r] * v1[r];
+            }
+        }
+        for (; q < cnt; ++q) {
+            a0 -= c[q] * ldw(V + (long long)q * N + i0);
+            if (h1) a1 -= c[q] * ldw(V + (long long)q * N + i1);
+        }
+        out[i0] = a0;
+        if (h1) out[i1] = a1;
+    }
 }
 
 // ks.red[k] = <a_k, b_k> for up to 8 pairs over the team partition.
@@ -244,8 +329,10 @@ FDE_NI bool arnoldi_right(const Team& t, const Inst& I, int lm, Combo<W> u, int 
     trace_mark(t, 11);
     plane_matvec_cols<W>(t, I, wk, z, W(1), epi_mvy<W>(I, tmp, out_store<W>(w)));
     trace_mark(t, 13);
-    return dots_own<W>(t, N, w, V, ks.vs, nd, true, ks,
-                       [&](auto f) { plane_cols_own_elements<W>(t, I, wk.bytes, f); });
+    // the column phase scatters each CTA's outputs over the plane: reduce over
+    // contiguous ranges instead, once every CTA's part is written
+    if (!team_sync(t)) return false;
+    return dots_basis<W>(t, N, w, V, ks.vs, nd, true, ks);
 }
 
 // ---------------------------------------------------------------------------
@@ -351,13 +438,13 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
             u.V = v.V;
             u.N = N;
             u.s = W(ks.vs[j]);
-            if (j == 0) {
-                u.base = v.V;
-            } else {
-                u.base = v.w;
-                u.c = kcoef<W>(ks);
-                u.cnt = ncoef;
-                u.store = v.V + (long long)j * N;
+            u.base = v.V + (long long)j * N;
+            if (j > 0) {
+                // V_j = w - sum_q coef_q V_q, streamed once; the transforms then
+                // read a plain vector
+                form_basis<W>(t, N, v.w, v.V, kcoef<W>(ks), ncoef, v.V + (long long)j * N);
+                if (!team_sync(t)) return false;
+                trace_mark(t, 25);
             }
             if (!arnoldi_right<W>(t, I, lm, u, j + 1, v.V, v.z, v.w, v.tt, ks, wk)) return false;
             st.iterations++;
@@ -392,12 +479,7 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
                     ks.y[threadIdx.x] = ks.red[threadIdx.x];
                 }
                 __syncthreads();
-                const W* kc = kcoef<W>(ks);
-                for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                    W acc = ldw(v.w + i);
-                    for (int q = 0; q <= j; ++q) acc -= kc[q] * ldw(v.V + (long long)q * N + i);
-                    v.w[i] = acc;
-                }
+                form_basis<W>(t, N, v.w, v.V, kcoef<W>(ks), j + 1, v.w);
                 __syncthreads();
                 if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
                 trace_mark(t, 31);

@@ -125,15 +125,37 @@ struct Mult {
 // Pack B real lines.  get(l, k, direct) returns r_k of line l.  COLMAJOR
 // maps consecutive threads to consecutive lines (coalesced for strided
 // columns).
+// Each thread gathers kUnroll elements before storing any, so their global
+// loads are in flight together (the getters only load).
+constexpr int kUnroll = 4;
+
 template <typename W, int EXT, bool COLMAJOR, typename GetF>
 FDE_D void cta_pack(cx<W>* buf, int B, int n, int Np, GetF get) {
     const int total = B * Np;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int l, m;
-        if (COLMAJOR) { l = idx % B; m = idx / B; }
-        else { m = idx % Np; l = idx / Np; }
-        auto g = [&](int k, bool direct) { return get(l, k, direct); };
-        buf[pad(l * Np + m)] = pack_elem<W, EXT>(g, m, n, Np);
+    const int nt = blockDim.x;
+    for (int base = threadIdx.x; base < total; base += kUnroll * nt) {
+        cx<W> v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = base + u * nt;
+            if (idx < total) {
+                int l, m;
+                if (COLMAJOR) { l = idx % B; m = idx / B; }
+                else { m = idx % Np; l = idx / Np; }
+                auto g = [&](int k, bool direct) { return get(l, k, direct); };
+                v[u] = pack_elem<W, EXT>(g, m, n, Np);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = base + u * nt;
+            if (idx < total) {
+                int l, m;
+                if (COLMAJOR) { l = idx % B; m = idx / B; }
+                else { m = idx % Np; l = idx / Np; }
+                buf[pad(l * Np + m)] = v[u];
+            }
+        }
     }
     __syncthreads();
 }
@@ -194,19 +216,26 @@ FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, con
 template <typename W, bool COLMAJOR, bool TWO, typename EpiF>
 FDE_D void cta_unpack(const cx<W>* buf, int B, int n, int Np, EpiF epi) {
     const int total = B * n;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        int l, p;
-        if (COLMAJOR) { l = idx % B; p = idx / B; }
-        else { p = idx % n; l = idx / n; }
-        const int k = p + 1;
-        const cx<W> q = buf[pad(l * Np + (k >> 1))];
-        const W va = (k & 1) ? q.y : q.x;
-        W vb = W(0);
-        if (TWO) {
-            const cx<W> q2 = buf[pad((B + l) * Np + (k >> 1))];
-            vb = (k & 1) ? q2.y : q2.x;
+    const int nt = blockDim.x;
+    for (int base = threadIdx.x; base < total; base += kUnroll * nt) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int idx = base + u * nt;
+            if (idx < total) {
+                int l, p;
+                if (COLMAJOR) { l = idx % B; p = idx / B; }
+                else { p = idx % n; l = idx / n; }
+                const int k = p + 1;
+                const cx<W> q = buf[pad(l * Np + (k >> 1))];
+                const W va = (k & 1) ? q.y : q.x;
+                W vb = W(0);
+                if (TWO) {
+                    const cx<W> q2 = buf[pad((B + l) * Np + (k >> 1))];
+                    vb = (k & 1) ? q2.y : q2.x;
+                }
+                epi(l, p, va, vb);
+            }
         }
-        epi(l, p, va, vb);
     }
 }
 

@@ -74,8 +74,8 @@ FDE_D Mult<W> mult_tau2(const Inst& I) {
 
 // ---------------------------------------------------------------------------
 // Inputs formed on the fly: u_p = s * (base_p - sum_q c_q V_q[p]) where V_q
-// are basis vectors at stride N.  `store` (optional) receives the
-// unscaled value base_p - sum ... on the element's direct read.
+// are vectors at stride N (the solution update of GMRES combines its basis
+// this way).
 // ---------------------------------------------------------------------------
 
 template <typename W>
@@ -86,7 +86,6 @@ struct Combo {
     int cnt;
     long long N;
     W s;
-    W* store;
     const W* pre;          // optional elementwise prescale applied after s (D^{-1} for P = D tau)
 
     // In the working precision: a basis update is a vector operation, not an
@@ -97,10 +96,8 @@ struct Combo {
         for (int q = 0; q < cnt; ++q) v -= c[q] * ldw(V + (long long)q * N + p);
         return v;
     }
-    FDE_D W get(long long p, bool direct) const {
-        const W r = raw(p);
-        if (direct && store) store[p] = r;
-        W v = s * r;
+    FDE_D W get(long long p, bool) const {
+        W v = s * raw(p);
         if (pre) v *= __ldg(pre + p);
         return v;
     }
@@ -251,7 +248,7 @@ FDE_NI void cta_matvec_1d(const Inst& I, const Wk& wk, const W* x, W s, Epi<W> e
 template <typename W>
 FDE_D int split_cols_per_unit(const AxisData& A, int team_size, int bytes) {
     const int cap_smem = max_lines<W>(A.P1, 2, bytes);
-    const int cap_fft = fft_lines_per_call(A.logP1, kThreads);
+    const int cap_fft = fft_lines_per_call(A.logP1, kThreads, (int)sizeof(W));
     const int cap = cap_smem < cap_fft ? cap_smem : cap_fft;
     int cc = 1;
     while (cc * team_size < A.P2) cc *= 2;          // units <= team size when possible
@@ -489,6 +486,7 @@ FDE_NI void plane_dst_rows(const Team& t, const Inst& I, const Wk& wk, Combo<W> 
         cta_pack<W, kExtOdd, false>(buf, nb, n1, Np, [&](int l, int k, bool d) {
             return u.get((long long)(row0 + l) * n1 + (k - 1), d);
         });
+        trace_mark(t, 70);
         fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
         cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
         for (int idx = threadIdx.x; idx < nb * n1; idx += blockDim.x) {
@@ -517,6 +515,7 @@ FDE_NI void plane_tau_cols(const Team& t, const Inst& I, const Wk& wk, W* z) {
         cta_pack<W, kExtOdd, true>(buf, nc, n2, Np, [&](int l, int k, bool) {
             return ldw(z + (long long)(k - 1) * n1 + c0 + l);
         });
+        trace_mark(t, 72);
         fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
         cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [&](int l) { return c0 + l; });
         fft_lines<W, true>(buf, A.logNp, nc, Np, wk.tw);
@@ -584,8 +583,11 @@ FDE_NI void plane_dst_matvec_rows(const Team& t, const Inst& I, const Wk& wk, co
         cta_pack<W, kExtOdd, false>(buf, nb, n1, Np, [&](int l, int k, bool) {
             return ldw(tprime + (long long)(row0 + l) * n1 + (k - 1));
         });
+        trace_mark(t, 74);
         fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
+        trace_mark(t, 90);
         cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
+        trace_mark(t, 91);
         for (int idx = threadIdx.x; idx < nb * n1; idx += blockDim.x) {
             const int l = idx / n1, p = idx - l * n1;
             const long long o = (long long)(row0 + l) * n1 + p;
@@ -595,10 +597,15 @@ FDE_NI void plane_dst_matvec_rows(const Team& t, const Inst& I, const Wk& wk, co
             z[o] = v;
         }
         __syncthreads();
+        trace_mark(t, 92);
         cta_pack<W, kExtZero, false>(buf, nb, n1, Np, [&](int l, int k, bool) { return sv[l * Np + k]; });
+        trace_mark(t, 93);
         fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
+        trace_mark(t, 94);
         cta_spectral<W>(buf, nb, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
+        trace_mark(t, 95);
         fft_lines<W, true>(buf, A.logNp, nbuf * nb, Np, wk.tw);
+        trace_mark(t, 96);
         auto epi = [&](int l, int p, W va, W vb) {
             const long long o = (long long)(row0 + l) * n1 + p;
             W v = c0 * sv[l * Np + p + 1] + coef(dp, I.dpc, o) * va;
@@ -639,6 +646,7 @@ FDE_NI void plane_matvec_cols(const Team& t, const Inst& I, const Wk& wk, const 
         cta_pack<W, kExtZero, true>(buf, nc, n2, Np, [&](int l, int k, bool) {
             return s * ldw(x + (long long)(k - 1) * n1 + c0 + l);
         });
+        trace_mark(t, 76);
         fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
         cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
         fft_lines<W, true>(buf, A.logNp, sym ? nc : 2 * nc, Np, wk.tw);
@@ -655,21 +663,6 @@ FDE_NI void plane_matvec_cols(const Team& t, const Inst& I, const Wk& wk, const 
     }
 }
 
-// Elements of the column units a CTA owns in plane_matvec_cols.
-template <typename W, typename F>
-FDE_D void plane_cols_own_elements(const Team& t, const Inst& I, int bytes, F f) {
-    const int C = plane_cols_per_unit<W>(I, t.size, bytes);
-    const int n1 = I.n1, n2 = I.n2;
-    const int units = (n1 + C - 1) / C;
-    for (int u = t.rank; u < units; u += t.size) {
-        const int c0 = u * C;
-        const int nc = (n1 - c0) < C ? (n1 - c0) : C;
-        for (int idx = threadIdx.x; idx < nc * n2; idx += blockDim.x) {
-            const int l = idx % nc, r = idx / nc;
-            f((long long)r * n1 + c0 + l);
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Operators (team barrier at the end)
