@@ -322,16 +322,16 @@ class Tau1D:
     def for_problem(prob: Problem1D, shift: bool = False, order: str = ORDER_TAU_D) -> "Tau1D":
         """P_F of Sec. 3.1: F = F_alpha(theta_j), D_n = (D_+ + D_-)/2.
 
-        shift=True is Case I (Sec. 3.1.1, constant d_+, d_-): the symbol becomes
-        F_alpha + 2 nu/(d_+ + d_-).
+        shift=True adds nu / dbar to the symbol, dbar the mean of D_n.  With
+        constant d_+, d_- this is Case I (Sec. 3.1.1): D_n = dbar I and
+        P = tau(F_alpha + 2 nu/(d_+ + d_-)) dbar = tau(nu + dbar F_alpha).  With
+        variable coefficients it is the same shift kept beside D_n (a variant
+        the paper does not tabulate; it leaves Case I's symbol unchanged).
         """
         F = scheme_symbol(prob.alpha, tau_grid(prob.n), prob.scheme)
         D = 0.5 * (prob.dp + prob.dm)
         if shift:
-            dsum = prob.dp + prob.dm
-            if not np.all(dsum == dsum[0]):
-                raise ValueError("the Case I shift needs constant coefficients")
-            F = F + 2.0 * prob.c0 / dsum[0]
+            F = F + prob.c0 / float(np.mean(D))
         return Tau1D(F=F, D=D, order=order)
 
     def tau_inv(self, r: np.ndarray) -> np.ndarray:

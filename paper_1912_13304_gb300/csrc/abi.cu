@@ -103,8 +103,10 @@ fde_status validate(const fde_problem* p, const fde_solve_opts* o) {
         if (!coeff_ok(p->ep, p->ep_const) || !coeff_ok(p->em, p->em_const)) return FDE_EINVAL;
     }
     if (p->tau_shift) {
-        if (p->dp || p->dm) return FDE_EINVAL;                          // constants only
-        if (!(p->dp_const + p->dm_const > 0.0)) return FDE_EINVAL;
+        // 1D: constants (Case I) or arrays (the shift c0/mean(D) beside D);
+        // 2D: constants only (P_hat)
+        if (p->dim == 2 && (p->dp || p->dm)) return FDE_EINVAL;
+        if (!p->dp && !p->dm && !(p->dp_const + p->dm_const > 0.0)) return FDE_EINVAL;
         if (p->dim == 2 && (p->ep || p->em || !(p->ep_const + p->em_const > 0.0))) return FDE_EINVAL;
     } else {
         // D = mean of the coefficients must be invertible; arrays are checked by the caller
@@ -122,7 +124,7 @@ fde_status validate(const fde_problem* p, const fde_solve_opts* o) {
         const bool symx = p->dp == p->dm && (p->dp != nullptr || p->dp_const == p->dm_const);
         const bool symy = p->dim == 1 || (p->ep == p->em && (p->ep != nullptr || p->ep_const == p->em_const));
         const bool constD = !p->dp && !p->dm && (p->dim == 1 || (!p->ep && !p->em));
-        if (!symx || !symy || !(p->tau_shift || constD)) return FDE_EINVAL;
+        if (!symx || !symy || !constD) return FDE_EINVAL;
     }
     return FDE_OK;
 }
@@ -131,14 +133,15 @@ struct Layout {
     size_t inst, sync, tw64, tw32;
     size_t lam64[2], lam32[2], phi64[2], phi32[2];
     size_t dinv64, dinv32, dp32, dm32, ep32, em32;
-    size_t r64, t64, wvec, split64, split32, wts;
+    size_t r64, t64, wvec, split64, split32, wts, dbar;
     size_t total;
     int TW, logTW;
     int Np[2];
     bool has_D;
 };
 
-bool compute_has_D(const fde_problem* p) { return !p->tau_shift; }
+// D^{-1} is applied unless the shifted symbol absorbs a constant D (Case I, P_hat).
+bool compute_has_D(const fde_problem* p) { return !p->tau_shift || (p->dim == 1 && (p->dp || p->dm)); }
 
 Layout layout(const fde_problem* p, const fde_solve_opts* o) {
     Layout L{};
@@ -178,6 +181,7 @@ Layout layout(const fde_problem* p, const fde_solve_opts* o) {
     L.split64 = take((size_t)2 * npmax * sizeof(cx<double>));
     L.split32 = take((size_t)2 * npmax * sizeof(cx<float>));
     L.wts = take((size_t)(npmax + 2) * sizeof(double));
+    L.dbar = take(sizeof(double));
     L.total = off;
     return L;
 }
@@ -200,6 +204,7 @@ struct AxisJob {
     double alpha;
     int kind;              // 0: 1D tau multiplier 1/(L (add + mult F)); 1: 2D axis part add + mult F
     double add, mult;
+    const double* dbar;    // kind 0 with a variable D: multiplier 1/(L (F + add / dbar))
     const cx<double>* tw64;
     cx<double>* lam64;
     cx<float>* lam32;
@@ -264,7 +269,8 @@ __global__ void __launch_bounds__(1024) k_axis(AxisJob J) {
         double v = 0.0;
         if (j >= 1 && j <= n) {
             const double F = symbol_sample(J.alpha, J.weights, j, Np);
-            v = J.kind == 0 ? invL / (J.add + J.mult * F) : J.add + J.mult * F;
+            if (J.kind == 0 && J.dbar) v = invL / (F + J.add / *J.dbar);
+            else v = J.kind == 0 ? invL / (J.add + J.mult * F) : J.add + J.mult * F;
         }
         J.phi64[j] = v;
         J.phi32[j] = (float)v;
@@ -304,6 +310,22 @@ __global__ void k_vectors(VecJob J) {
             J.dinv32[i] = (float)di;
         }
     }
+}
+
+// dbar = mean of D = (d_+ + d_-)/2 over the line, in a fixed summation order
+// (one block: strided per-thread sums, then a shared-memory tree).
+__global__ void __launch_bounds__(1024) k_mean_d(long long N, const double* dp, const double* dm, double dpc,
+                                                 double dmc, double* dbar) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < N; i += blockDim.x) s += 0.5 * ((dp ? dp[i] : dpc) + (dm ? dm[i] : dmc));
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *dbar = red[0] / (double)N;
 }
 
 __global__ void k_write_inst(Inst v, Inst* dst) { *dst = v; }
@@ -547,10 +569,17 @@ fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* op
         J.weights = prob->weights;
         J.alpha = a == 0 ? prob->alpha : prob->beta;
         if (prob->dim == 1) {
-            // P_F (Sec. 3.1): 1/(L F); Case I (Sec. 3.1.1): D tau(F + 2 nu/(d_+ + d_-)) = tau(nu + dbar F)
+            // P_F (Sec. 3.1): 1/(L F); Case I (Sec. 3.1.1): D tau(F + 2 nu/(d_+ + d_-)) = tau(nu + dbar F);
+            // with variable coefficients the shift nu/mean(D) stays beside D
             J.kind = 0;
             J.add = shift ? I.c0 : 0.0;
             J.mult = shift ? dbar : 1.0;
+            if (shift && (prob->dp || prob->dm)) {
+                double* dbar_dev = at<double>(workspace, Lo.dbar);
+                k_mean_d<<<1, 1024, 0, st>>>(I.N, prob->dp, prob->dm, prob->dp_const, prob->dm_const, dbar_dev);
+                J.dbar = dbar_dev;
+                J.mult = 1.0;
+            }
         } else {
             // Sec. 3.2: F = F_a + sr F_b, or P_hat's c0 + d F_a + sr e F_b, split per axis
             J.kind = 1;

@@ -86,9 +86,17 @@ def test_pcg_needs_symmetric_constant_problem(L):
     assert st == fde.OK
 
 
-def test_shift_needs_constant_coefficients(L):
-    o = fde.make_opts()
-    st, _ = _ws(fde.make_problem(1, 255, 1.5, 0.01, dp=1 << 20, dm=1 << 20, tau_shift=True), o)
+def test_shift_with_variable_coefficients_1d_gmres_only(L):
+    # 1D: the shift c0/mean(D) beside a variable D is a GMRES preconditioner
+    st, _ = _ws(fde.make_problem(1, 255, 1.5, 0.01, dp=1 << 20, dm=1 << 20, tau_shift=True), fde.make_opts())
+    assert st == fde.OK
+    # ... not symmetric, so not for PCG
+    st, _ = _ws(fde.make_problem(1, 255, 1.5, 0.01, dp=1 << 20, dm=1 << 20, tau_shift=True),
+                fde.make_opts(method="pcg"))
+    assert st == fde.EINVAL
+    # 2D: P_hat needs constant coefficients
+    st, _ = _ws(fde.make_problem(2, 255, 1.5, 0.01, n2=255, beta=1.5, dp=1 << 20, dm=1 << 20, tau_shift=True),
+                fde.make_opts())
     assert st == fde.EINVAL
 
 

@@ -42,8 +42,8 @@ def make_1d(gpu, n, kind, alpha=1.5, dt=1 / 512, weights="gl1", shift=False, ord
         plan = fde.Plan(1, n, alpha, dt, dp_const=dp[0], dm_const=dm[0], weights=weights, tau_shift=shift,
                         order=order, precision=precision)
     else:
-        plan = fde.Plan(1, n, alpha, dt, dp=dp, dm=dm if kind == "var" else dp, weights=weights, order=order,
-                        precision=precision)
+        plan = fde.Plan(1, n, alpha, dt, dp=dp, dm=dm if kind == "var" else dp, weights=weights, tau_shift=shift,
+                        order=order, precision=precision)
     prob = oracle.Problem1D(alpha=alpha, n=n, c0=h ** alpha / dt, dp=dp, dm=dm, scheme=weights)
     return plan, prob
 
@@ -84,6 +84,19 @@ def test_tau_1d(gpu, n, variant, dtype):
     plan, prob = make_1d(gpu, n, kind, shift=variant == "shift", order="d_tau" if variant == "d_tau" else "tau_d")
     P = oracle.Tau1D.for_problem(prob, shift=variant == "shift", order="d_tau" if variant == "d_tau" else "tau_d")
     r = np.random.default_rng(n + 1).uniform(-1, 1, n)
+    z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
+    assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("order", ["tau_d", "d_tau"])
+@pytest.mark.parametrize("n", [7, 1023, 4095, 16383, 65535])
+def test_tau_1d_shifted_variable_coefficients(gpu, n, order, dtype):
+    # the shift c0/mean(D) beside a variable D (assembled on the device: the
+    # mean is a device reduction), every line layout
+    plan, prob = make_1d(gpu, n, "var", shift=True, order=order)
+    P = oracle.Tau1D.for_problem(prob, shift=True, order=order)
+    r = np.random.default_rng(n + 5).uniform(-1, 1, n)
     z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
     assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
 

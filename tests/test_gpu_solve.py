@@ -66,6 +66,24 @@ def test_gmres_right_variable_coefficients(gpu, n, alpha):
     assert rel_err(info2["x"].cpu().numpy(), tight.x) < 1e-8
 
 
+@pytest.mark.parametrize("alpha", [1.2, 1.8])
+@pytest.mark.parametrize("n", [1023, 16383])
+def test_gmres_shifted_variable_coefficients(gpu, n, alpha):
+    # the shifted variant on the variable-coefficient workload: iterations
+    # within +-1 of the oracle's and far fewer than the unshifted P_F's
+    w = workloads.config2(n=n, alphas=(alpha,))[0]
+    prob = oracle_problem_1d(w)
+    b = prob.c0 * w["u0"]
+    ref = oracle.gmres(prob.matvec, b, Pinv=oracle.Tau1D.for_problem(prob, shift=True).apply_inverse, x0=w["u0"],
+                       restart=30, tol=1e-8)
+    plan = fde.Plan.from_workload(w, shift=True)
+    info = plan.solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8)
+    assert info["status"] == fde.OK, info
+    assert abs(info["iterations"] - ref.iterations) <= 1, (info["iterations"], ref.iterations)
+    x = info["x"].cpu().numpy()
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+
+
 @pytest.mark.parametrize("tol", [1e-10, 1e-12])
 @pytest.mark.parametrize("n", [255, 4095, 16383])
 def test_gmres_right_tight_tolerance_iterations(gpu, n, tol):

@@ -345,6 +345,28 @@ def test_case1_shifted_pcg_iterations_bounded_in_n():
     assert max(its) <= 6 and max(its) - min(its) <= 1, its
 
 
+def test_shifted_variable_coefficient_variant_bounded_and_cheaper():
+    """The shift nu/dbar kept beside a variable D (the variable-coefficient
+    generalisation of Case I) on the variable-coefficient workload shape at
+    alpha = 1.2, where nu dominates the lowest symbol samples: GMRES
+    iterations grow at most logarithmically in n (8, 11, 13 for n = 255,
+    1023, 4095) and stay below half those of the unshifted P_F (29, 38, 44)."""
+    import workloads
+    its_s, its_u = [], []
+    for n in (255, 1023, 4095):
+        w = workloads.config2(n=n, alphas=(1.2,))[0]
+        h = 1.0 / (n + 1)
+        prob = Problem1D(alpha=1.2, n=n, c0=h ** 1.2 / w["dt"], dp=w["dp"], dm=w["dm"])
+        b = prob.c0 * w["u0"]
+        for shift, its in ((True, its_s), (False, its_u)):
+            P = Tau1D.for_problem(prob, shift=shift)
+            res = gmres(prob.matvec, b, Pinv=P.apply_inverse, restart=30, tol=1e-8, maxiter=2000)
+            assert res.converged
+            its.append(res.iterations)
+    assert its_s == sorted(its_s) and its_s[-1] - its_s[0] <= 6 and its_s[-1] <= 16, its_s
+    assert all(s * 2 <= u for s, u in zip(its_s, its_u)), (its_s, its_u)
+
+
 def test_2d_shifted_pcg_iterations_bounded_in_n():
     """Theorem 3: P_hat gives a spectrum bounded independently of N."""
     its = []
