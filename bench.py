@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--graph", type=int, default=1, help="1: replay the time-step loop as a CUDA graph")
     ap.add_argument("--batch", type=int, default=1, help="1: also time the 256-instance batched workload")
     ap.add_argument("--two-d", type=int, default=1, help="1: also time the two 2D workloads")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: pick each plan's transform schedule with fde_autotune before timing")
     ap.add_argument("--variants", type=int, default=1,
                     help="1: also time the shifted preconditioner variant (c0/mean(D) beside D) in FP64")
     ap.add_argument("--balance", type=int, default=1,
@@ -165,6 +167,7 @@ def run_ours(args, rank, world, device):
     for prec, shift in runs:
         key = prec + ("+shift" if shift else "")
         plans = [fde.Plan.from_workload(w, precision=prec, shift=shift, device=device) for w in ws]
+        schedule = [p.autotune() for p in plans][0] if args.autotune else (0, 0)
         u = [torch.empty(n, dtype=torch.float64, device=device) for _ in ws]
         kw = dict(tol=TOL, max_iters=20000, inner_tol=args.inner_tol, max_outer=200, balance=bool(args.balance))
         u0_dev = [x.to(device) for x in u0_host]
@@ -250,7 +253,7 @@ def run_ours(args, rank, world, device):
             unknown_iters_per_s=n * its / (t_step * 1e-3), iterations=its,
             outer=sum(i["outer"] for i in infos), worst_relres=worst, converged=ok,
             e2e_ms=sum(e2e_ms) / len(e2e_ms), roofline=roof, clocks=clk.summary(),
-            launch_ms=avg_launch, step_ms=step_ms)
+            launch_ms=avg_launch, step_ms=step_ms, schedule={"ctas": schedule[0], "log_p1": schedule[1]})
         for p in plans:
             p.close()
     return results
@@ -270,12 +273,10 @@ def run_batch(args, device):
     ws = workloads.config4()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     out = {}
-    runs = [(p, False) for p in args.precisions.split(",") if p]
-    if args.variants:
-        runs.append(("f64", True))
-    for prec, shift in runs:
-        key = prec + ("+shift" if shift else "")
-        plans = [fde.Plan.from_workload(w, precision=prec, shift=shift, device=device) for w in ws]
+    # the workload's own preconditioner (Case I shift) and the default layout:
+    # one-CTA teams hold whole lines where they fit
+    for prec in [p for p in args.precisions.split(",") if p]:
+        plans = [fde.Plan.from_workload(w, precision=prec, device=device) for w in ws]
         bs = [p.c0 * torch.tensor(w["b"], dtype=torch.float64, device=device) for p, w in zip(plans, ws)]
         xs = [torch.zeros_like(b) for b in bs]
         info = torch.zeros(len(ws) * fde.INFO_BYTES, dtype=torch.uint8, device=device)
@@ -305,7 +306,11 @@ def run_batch(args, device):
         infos = fde.decode_info(info.cpu().numpy().tobytes(), len(ws))
         t = sum(ms) / len(ms)
         unk = sum(w["n1"] * i["iterations"] for w, i in zip(ws, infos))
+        by_n = {}
+        for w, i in zip(ws, infos):
+            by_n.setdefault(w["n1"], []).append(i["iterations"])
         out[prec] = {"ms_per_launch": t, "solves_per_s": len(ws) / (t * 1e-3),
+                     "max_iterations_by_n": {str(k): max(v) for k, v in sorted(by_n.items())},
                      "unknown_iters_per_s": unk / (t * 1e-3),
                      "iterations": sum(i["iterations"] for i in infos),
                      "outer": sum(i["outer"] for i in infos),
@@ -349,6 +354,7 @@ def run_2d(args, device):
         N = w["n1"] * w["n2"]
         for prec in [p for p in args.precisions.split(",") if p]:
             plan = fde.Plan.from_workload(w, precision=prec, device=device)
+            schedule = plan.autotune() if args.autotune else (0, 0)
             if w["rhs_scale"] == "unit":
                 b = plan.c0 * torch.tensor(w["b"], dtype=torch.float64, device=device)
                 x0 = torch.zeros_like(b)
@@ -381,6 +387,7 @@ def run_2d(args, device):
                          "unknown_iters_per_s": N * inf["iterations"] / (t * 1e-3),
                          "iterations": inf["iterations"], "outer": inf["outer"], "relres": inf["relres"],
                          "converged": inf["status"] == fde.OK and inf["relres"] <= TOL,
+                         "schedule": {"ctas": schedule[0], "log_p1": schedule[1]},
                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                       "frac": gbs / hbm_peak, "traffic": None}}
             plan.close()
@@ -495,7 +502,8 @@ def main():
             "gpu_launches": (TIME_STEPS * (len(ALPHAS) + 1 + (1 if args.balance else 0))) * args.steps,
             "roofline": head["roofline"], "clocks": head["clocks"],
             "paths": {k: {kk: v[kk] for kk in ("ms_per_step", "solves_per_s", "unknown_iters_per_s", "iterations",
-                                                "outer", "worst_relres", "converged", "roofline", "launch_ms")}
+                                                "outer", "worst_relres", "converged", "roofline", "launch_ms",
+                                                "schedule")}
                       for k, v in res.items()},
         }
         if batch is not None:

@@ -206,6 +206,35 @@ fde_status fde_step_rhs(const fde_plan* plan, const double* u_prev, const double
 #define FDE_MATVEC_NOALLOC_SCRATCH_BYTES 640256
 fde_status fde_toeplitz_matvec_noalloc(const fde_problem* prob, const double* x, double* y, void* stream);
 
+/*
+ * Transform schedule of a plan (no counterpart in the paper; the paper fixes
+ * the method, not its mapping to the GPU).
+ *   ctas:   CTAs that cooperate on this plan in single-plan solves and operator
+ *           calls (0 = all co-resident CTAs); batched solves size their teams
+ *           themselves.
+ *   log_p1: 1D only.  0: a CTA holds each whole line where it fits in shared
+ *           memory (else the line is split with P1 = 2^floor(log2(n1+1)/2));
+ *           k >= 4: the line is split across the CTAs as a four-step FFT of
+ *           n1 + 1 = P1 x P2 points, P1 = 2^k <= P2.  2D: must be 0.
+ * FDE_EINVAL if the split does not fit shared memory for the plan's
+ * precisions.  Rewrites the device copy of the plan on `stream`.
+ */
+fde_status fde_plan_set_schedule(fde_plan* plan, int ctas, int log_p1, void* stream);
+
+/*
+ * Autotuner (no counterpart in the paper): times one tau solve plus one
+ * matvec -- the operators of an iteration -- in the plan's solver precision
+ * on the plan's own scratch vectors for every feasible schedule
+ * (fde_plan_set_schedule: ctas in {16, 32, 64, ..., all}; 1D: whole lines per
+ * CTA, and every split 2^4 <= P1 <= P2) and keeps the fastest.  The choice is
+ * cached per (dim, n1, n2, precision, method, restart) for the process, so a
+ * later plan of the same shape takes it without timing.  Synchronises
+ * `stream` (CUDA events); allocates no device memory; overwrites the plan's
+ * Krylov scratch (call it between solves).  *ctas and *log_p1 (may be NULL)
+ * receive the choice.
+ */
+fde_status fde_autotune(fde_plan* plan, void* stream, int* ctas, int* log_p1);
+
 /* Scalars the plan derived from the problem: c0, sr, h1^alpha. */
 fde_status fde_plan_scalars(const fde_plan* plan, double* c0, double* sr, double* h_alpha);
 

@@ -84,6 +84,10 @@ def lib() -> ctypes.CDLL:
         L.fde_assemble_symbol.restype = cint
         L.fde_toeplitz_matvec.argtypes = [vp, cint, vp, vp, vp]
         L.fde_toeplitz_matvec.restype = cint
+        L.fde_plan_set_schedule.argtypes = [vp, cint, cint, vp]
+        L.fde_plan_set_schedule.restype = cint
+        L.fde_autotune.argtypes = [vp, vp, P(cint), P(cint)]
+        L.fde_autotune.restype = cint
         L.fde_toeplitz_matvec_noalloc.argtypes = [P(FdeProblem), vp, vp, vp]
         L.fde_toeplitz_matvec_noalloc.restype = cint
         L.fde_tau_solve.argtypes = [vp, cint, vp, vp, vp]
@@ -190,6 +194,16 @@ def assemble_symbol(problem: FdeProblem, opts: FdeSolveOpts, workspace, nbytes: 
 
 def toeplitz_matvec(plan: int, dtype: int, x, y, stream=None):
     _check(lib().fde_toeplitz_matvec(plan, dtype, _ptr(x), _ptr(y), _stream(stream)), "fde_toeplitz_matvec")
+
+
+def plan_set_schedule(plan: int, ctas: int, log_p1: int, stream=None):
+    _check(lib().fde_plan_set_schedule(plan, ctas, log_p1, _stream(stream)), "fde_plan_set_schedule")
+
+
+def autotune(plan: int, stream=None) -> tuple[int, int]:
+    c, l = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().fde_autotune(plan, _stream(stream), ctypes.byref(c), ctypes.byref(l)), "fde_autotune")
+    return c.value, l.value
 
 
 MATVEC_NOALLOC_MAX_N = 4095

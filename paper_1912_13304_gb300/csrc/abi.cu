@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -23,6 +24,7 @@ struct fde_plan {
     int device;
     int smem_bytes;
     int grid[3];            // co-resident CTAs of each engine mode
+    int ctas;               // CTAs of single-plan launches (0: all co-resident)
 };
 
 namespace {
@@ -654,6 +656,7 @@ static fde_status launch_op(const fde_plan* p, int op, int dtype, const void* in
     const int mode = dtype == FDE_F64 ? kModeF64 : kModeF32;
     const int lm = dtype == FDE_F64 ? (p->inst.line_mode & 0xff) : ((p->inst.line_mode >> 8) & 0xff);
     int grid = p->grid[mode];
+    if (p->ctas > 0 && p->ctas < grid) grid = p->ctas;
     if (p->inst.dim == 1 && lm == kLineCta) grid = 1;
     a->team_size = grid;
     cudaError_t e = cudaMemsetAsync(p->sync_dev, 0, offsetof(SyncArea, partial), st);
@@ -721,6 +724,9 @@ fde_status fde_krylov_solve(const fde_plan* const* plans, int count, const doubl
     } else if (count >= G) {
         ts = 1;
         grid = G;
+    } else if (count == 1 && p0->ctas > 0 && p0->ctas < G) {
+        ts = p0->ctas;          // a schedule chosen by fde_plan_set_schedule / fde_autotune
+        grid = ts;
     } else {
         ts = G / count;
         grid = ts * count;
@@ -953,4 +959,184 @@ extern "C" fde_status fde_toeplitz_matvec_noalloc(const fde_problem* prob, const
     M.buf = reinterpret_cast<cx<double>*>(s + kNoalloc.buf);
     k_line_matvec<<<1, 1024, 0, st>>>(M);
     return cudaGetLastError() == cudaSuccess ? FDE_OK : FDE_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Transform schedules: CTAs per plan, and the layout of a 1D line
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Work bytes of one CTA beside the Krylov scalars and a twiddle table of 2^logT.
+int work_bytes_for(const fde_plan* p, int logT) {
+    const int m = p->opts.method == FDE_GMRES ? p->opts.restart : 1;
+    return p->smem_bytes - (int)kshared_bytes(m, logT);
+}
+
+// Can a line of Np = 2^(logP1 + logP2) be split as P1 x P2 in the four-step
+// layout with elements of esz bytes (complex)?  Rows hold two lines plus a
+// second output set; columns need at least one line.
+bool split_feasible(const fde_plan* p, int logP1, int logP2, int esz) {
+    if (logP1 < 4 || logP1 > logP2 || logP2 > kMaxLogTsm) return false;
+    const int logT = logP2;
+    const int work = work_bytes_for(p, logT);
+    if (fft_lines_per_call(logP2, kThreads, esz / 2) < 1 || fft_lines_per_call(logP1, kThreads, esz / 2) < 1)
+        return false;
+    return (long long)padded_len(4 << logP2) * esz <= work && (long long)padded_len(2 << logP1) * esz <= work;
+}
+
+}  // namespace
+
+extern "C" fde_status fde_plan_set_schedule(fde_plan* p, int ctas, int log_p1, void* stream) {
+    if (!p || ctas < 0 || log_p1 < 0) return FDE_EINVAL;
+    Inst I = p->inst;
+    if (I.dim == 2) {
+        if (log_p1 != 0) return FDE_EINVAL;
+    } else {
+        AxisData& A = I.ax[0];
+        const int m = p->opts.method == FDE_GMRES ? p->opts.restart : 1;
+        const int work_max = p->smem_bytes - (int)kshared_bytes(m, kMaxLogTsm);
+        int lm64, lm32, logP1;
+        if (log_p1 == 0) {
+            // whole lines in one CTA where they fit, else the balanced split
+            Layout Lo{};
+            Lo.Np[0] = A.Np;
+            const int lmodes = line_modes(&p->prob, Lo, work_max);
+            lm64 = lmodes & 0xff;
+            lm32 = (lmodes >> 8) & 0xff;
+            logP1 = A.logNp / 2;
+        } else {
+            // both element sizes: the operator calls take either dtype on any plan
+            const int logP2 = A.logNp - log_p1;
+            if (!split_feasible(p, log_p1, logP2, (int)sizeof(cx<double>)) ||
+                !split_feasible(p, log_p1, logP2, (int)sizeof(cx<float>)))
+                return FDE_EINVAL;
+            lm64 = lm32 = kLineSplit;
+            logP1 = log_p1;
+        }
+        A.logP1 = logP1;
+        A.logP2 = A.logNp - logP1;
+        A.P1 = 1 << A.logP1;
+        A.P2 = 1 << A.logP2;
+        I.line_mode = lm64 | (lm32 << 8);
+        const bool any_cta = lm64 == kLineCta || lm32 == kLineCta;
+        int lg = any_cta ? A.logNp : A.logP2;
+        if (lg > kMaxLogTsm) lg = kMaxLogTsm;
+        I.logTsm = lg < 2 ? 2 : lg;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_write_inst<<<1, 1, 0, st>>>(I, p->inst_dev);
+    if (cudaGetLastError() != cudaSuccess) return FDE_ECUDA;
+    p->inst = I;
+    p->ctas = ctas;
+    return FDE_OK;
+}
+
+namespace {
+
+struct TuneKey {
+    int dim, n1, n2, precision, method, restart;
+    bool operator<(const TuneKey& o) const {
+        const int a[6] = {dim, n1, n2, precision, method, restart};
+        const int b[6] = {o.dim, o.n1, o.n2, o.precision, o.method, o.restart};
+        for (int i = 0; i < 6; ++i)
+            if (a[i] != b[i]) return a[i] < b[i];
+        return false;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+// Mean time of one tau solve + one matvec (the operators of an iteration) in ms.
+fde_status time_schedule(fde_plan* p, int dtype, void* in, void* out, cudaStream_t st, float* ms) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return FDE_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return FDE_ECUDA;
+    }
+    fde_status s = FDE_OK;
+    const int reps = 3;
+    for (int r = 0; r < 1 + reps && s == FDE_OK; ++r) {
+        if (r == 1 && cudaEventRecord(e0, st) != cudaSuccess) s = FDE_ECUDA;
+        if (s == FDE_OK) s = launch_op(p, kOpTau, dtype, in, out, st);
+        if (s == FDE_OK) s = launch_op(p, kOpMatvec, dtype, out, in, st);
+    }
+    if (s == FDE_OK && cudaEventRecord(e1, st) != cudaSuccess) s = FDE_ECUDA;
+    if (s == FDE_OK && cudaEventSynchronize(e1) != cudaSuccess) s = FDE_ECUDA;
+    if (s == FDE_OK && cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) s = FDE_ECUDA;
+    if (s == FDE_OK) *ms /= (float)reps;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+}
+
+}  // namespace
+
+extern "C" fde_status fde_autotune(fde_plan* p, void* stream, int* ctas_out, int* log_p1_out) {
+    if (!p) return FDE_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const TuneKey key{p->prob.dim, p->prob.n1, p->prob.dim == 2 ? p->prob.n2 : 1, p->opts.precision,
+                      p->opts.method, p->opts.restart};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            const fde_status s = fde_plan_set_schedule(p, it->second.first, it->second.second, stream);
+            if (s == FDE_OK) {
+                if (ctas_out) *ctas_out = it->second.first;
+                if (log_p1_out) *log_p1_out = it->second.second;
+            }
+            return s;
+        }
+    }
+    const int dtype = p->opts.precision == FDE_PREC_F64 ? FDE_F64 : FDE_F32;
+    const int mode = dtype == FDE_F64 ? kModeF64 : kModeF32;
+    const int G = p->grid[mode];
+    // scratch: the plan's FP64 residual vector (N doubles also hold N floats) and
+    // its first Krylov vector; the operators' own 2D scratch is t64
+    void* in = p->inst.r64;
+    void* out = p->inst.wvec;
+    if (cudaMemsetAsync(in, 0, (size_t)p->inst.N * sizeof(double), st) != cudaSuccess) return FDE_ECUDA;
+    std::vector<int> team;
+    for (int c = 16; c < G; c *= 2) team.push_back(c);
+    team.push_back(G);
+    std::vector<std::pair<int, int>> cand;
+    if (p->inst.dim == 2) {
+        for (int c : team) cand.push_back({c, 0});
+    } else {
+        cand.push_back({0, 0});                       // whole lines per CTA where they fit
+        const int logNp = p->inst.ax[0].logNp;
+        for (int l1 = 4; 2 * l1 <= logNp; ++l1)
+            for (int c : team) cand.push_back({c, l1});
+    }
+    const int saved_ctas = p->ctas;
+    const int saved_lp1 = p->inst.ax[0].logP1;
+    const bool saved_split = p->inst.dim == 1 &&
+        ((dtype == FDE_F64 ? p->inst.line_mode & 0xff : (p->inst.line_mode >> 8) & 0xff) == kLineSplit);
+    float best = 0.0f;
+    std::pair<int, int> pick{-1, -1};
+    for (const auto& c : cand) {
+        if (fde_plan_set_schedule(p, c.first, c.second, stream) != FDE_OK) continue;   // infeasible
+        float ms = 0.0f;
+        const fde_status s = time_schedule(p, dtype, in, out, st, &ms);
+        if (s != FDE_OK) return s;
+        if (pick.first < 0 || ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    if (pick.first < 0) {
+        fde_plan_set_schedule(p, saved_ctas, saved_split ? saved_lp1 : 0, stream);
+        return FDE_ECUDA;
+    }
+    const fde_status s = fde_plan_set_schedule(p, pick.first, pick.second, stream);
+    if (s != FDE_OK) return s;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = pick;
+    }
+    if (ctas_out) *ctas_out = pick.first;
+    if (log_p1_out) *log_p1_out = pick.second;
+    return FDE_OK;
 }

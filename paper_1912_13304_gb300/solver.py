@@ -6,8 +6,8 @@ from __future__ import annotations
 
 from typing import Optional, Sequence
 
-from . import (F32, F64, INFO_BYTES, assemble_symbol, decode_info, krylov_solve, make_opts, make_problem,
-               plan_destroy, plan_scalars, step_rhs, tau_solve, toeplitz_matvec, workspace_size)
+from . import (F32, F64, INFO_BYTES, assemble_symbol, autotune, decode_info, krylov_solve, make_opts, make_problem,
+               plan_destroy, plan_scalars, plan_set_schedule, step_rhs, tau_solve, toeplitz_matvec, workspace_size)
 
 
 def _torch():
@@ -100,6 +100,15 @@ class Plan:
         info = solve_batch([self], [b], [x], **kw)[0]
         info["x"] = x
         return info
+
+    def set_schedule(self, ctas: int = 0, log_p1: int = 0, stream=None):
+        """Fix the transform schedule (fde_plan_set_schedule)."""
+        plan_set_schedule(self.handle, ctas, log_p1, stream)
+
+    def autotune(self, stream=None) -> tuple[int, int]:
+        """Time the feasible schedules and keep the fastest (fde_autotune):
+        returns (ctas, log_p1)."""
+        return autotune(self.handle, stream)
 
     def close(self):
         if getattr(self, "handle", 0):

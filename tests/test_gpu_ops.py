@@ -192,3 +192,47 @@ def test_step_rhs(gpu):
     h = 1.0 / (n + 1)
     ref = prob.c0 * u + h ** 1.5 * f
     assert rel_err(b, ref) < 1e-15
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n", [4095, 16383, 65535])
+def test_every_split_schedule_1d(gpu, n, dtype):
+    # every four-step factorisation n + 1 = P1 x P2 the shared memory admits,
+    # with a small and the full team, gives the same operators
+    plan, prob = make_1d(gpu, n, "var", alpha=1.7)
+    P = oracle.Tau1D.for_problem(prob)
+    rng = np.random.default_rng(n + 2)
+    x = rng.uniform(-1, 1, n)
+    rows = np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 30)])
+    ref_rows = prob.matvec_rows(x, rows)
+    scale = np.max(np.abs(prob.matvec_rows(x, rng.integers(0, n, 100))))
+    z_ref = P.apply_inverse(x)
+    logn = int(np.log2(n + 1))
+    tried = 0
+    for lp1 in range(4, logn // 2 + 1):
+        for ctas in (16, 0):
+            try:
+                plan.set_schedule(ctas, lp1)
+            except fde.FdeError as e:
+                assert e.status == fde.EINVAL
+                continue
+            tried += 1
+            y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
+            assert np.max(np.abs(y[rows] - ref_rows)) / scale < TOL[("mv", dtype)], (lp1, ctas)
+            z = plan.tau(to_dev(gpu, x, dtype)).double().cpu().numpy()
+            assert rel_err(z, z_ref) < TOL[("tau", dtype)], (lp1, ctas)
+    assert tried >= 2
+    plan.set_schedule(0, 0)
+    y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
+    assert np.max(np.abs(y[rows] - ref_rows)) / scale < TOL[("mv", dtype)]
+
+
+def test_schedule_validation(gpu):
+    plan, _ = make_1d(gpu, 1023, "var")
+    for bad in ((-1, 0), (0, -1), (0, 3), (0, 6)):     # 2^6 > sqrt(1024): P1 > P2
+        with pytest.raises(fde.FdeError):
+            plan.set_schedule(*bad)
+    plan2, _ = make_2d(gpu, 63, 63, "var")
+    with pytest.raises(fde.FdeError):
+        plan2.set_schedule(0, 4)
+    plan2.set_schedule(16, 0)

@@ -340,3 +340,50 @@ def test_batched_256_instances_full_size(gpu, precision):
             assert abs(infos[i]["iterations"] - ref.iterations) <= 1, (w["n1"], infos[i], ref.iterations)
         x = xs[i].cpu().numpy()
         assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8, (w["n1"], infos[i])
+
+
+def test_autotuned_schedule_solves_match_oracle(gpu):
+    n = 16383
+    w = workloads.config2(n=n, alphas=(1.5,))[0]
+    prob = oracle_problem_1d(w)
+    b = prob.c0 * w["u0"]
+    ref = oracle.gmres(prob.matvec, b, Pinv=oracle.Tau1D.for_problem(prob).apply_inverse, x0=w["u0"], restart=30,
+                       tol=1e-8)
+    plan = fde.Plan.from_workload(w)
+    ctas, lp1 = plan.autotune()
+    info = plan.solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8)
+    assert info["status"] == fde.OK, (info, ctas, lp1)
+    assert abs(info["iterations"] - ref.iterations) <= 1, (info["iterations"], ref.iterations, ctas, lp1)
+    x = info["x"].cpu().numpy()
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+    # a second plan of the same shape takes the cached choice
+    plan2 = fde.Plan.from_workload(w)
+    assert plan2.autotune() == (ctas, lp1)
+
+
+def test_autotuned_schedule_full_size_and_2d(gpu):
+    # n = 65535: the tuned schedule against the default one (same iterations)
+    w = workloads.config2(alphas=(1.8,))[0]
+    infos = []
+    for tune in (False, True):
+        plan = fde.Plan.from_workload(w)
+        if tune:
+            plan.autotune()
+        b = plan.rhs(to_dev(gpu, w["u0"], "f64"))
+        infos.append(plan.solve(b, x=to_dev(gpu, w["u0"], "f64"), tol=1e-8))
+    assert all(i["status"] == fde.OK and i["relres"] <= 1e-8 for i in infos), infos
+    assert abs(infos[0]["iterations"] - infos[1]["iterations"]) <= 1
+    # 2D: team size only
+    w2 = workloads.config5(n=255, steps=1)
+    plan = fde.Plan.from_workload(w2, precision="f32_ir")
+    ctas, lp1 = plan.autotune()
+    assert lp1 == 0 and ctas >= 16
+    h = 1.0 / 256
+    prob = oracle.Problem2D(alpha=w2["alpha"], beta=w2["beta"], n1=255, n2=255, c0=h ** w2["alpha"] / w2["dt"],
+                            sr=h ** w2["alpha"] / h ** w2["beta"], dp=w2["dp"], dm=w2["dm"], ep=w2["ep"],
+                            em=w2["em"], scheme="wsgd2")
+    b = prob.c0 * w2["u0"]
+    info = plan.solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w2["u0"], "f64"), tol=1e-8, inner_tol=1e-4)
+    assert info["status"] == fde.OK, info
+    x = info["x"].cpu().numpy()
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
