@@ -56,7 +56,9 @@ typedef enum {
 
 typedef enum { FDE_F64 = 0, FDE_F32 = 1 } fde_dtype;
 typedef enum { FDE_WEIGHTS_GL1 = 0, FDE_WEIGHTS_WSGD2 = 1 } fde_weights;
-typedef enum { FDE_ORDER_TAU_D = 0, FDE_ORDER_D_TAU = 1 } fde_order;
+/* P = tau(F) D, P = D tau(F) (Sec. 3.1), or P_F-tilde = S diag(D_j F(theta_j)) S
+   (Sec. 4, Table 2; 1D): D sampled on the tau grid and folded into the symbol. */
+typedef enum { FDE_ORDER_TAU_D = 0, FDE_ORDER_D_TAU = 1, FDE_ORDER_TAU_DF = 2 } fde_order;
 typedef enum { FDE_SCHEME_IMPLICIT_EULER = 0, FDE_SCHEME_CRANK_NICOLSON = 1 } fde_scheme;
 typedef enum { FDE_PCG = 0, FDE_GMRES = 1 } fde_method;
 typedef enum {
@@ -82,7 +84,7 @@ typedef struct {
     const double *dp, *dm, *ep, *em;        /* d_+, d_-, e_+, e_- (device) or NULL */
     double dp_const, dm_const, ep_const, em_const;
     int tau_shift;         /* 1: shifted symbol (needs constant, equal coefficients) */
-    int order;             /* fde_order: P = tau(F) D (default) or D tau(F) */
+    int order;             /* fde_order: P = tau(F) D (default), D tau(F), or P_F-tilde (1D, no shift) */
 } fde_problem;
 
 typedef struct {
@@ -165,8 +167,12 @@ fde_status fde_krylov_solve(const fde_plan* const* plans, int count, const doubl
                             fde_solve_info* info_dev, void* stream);
 
 /*
- * Right-hand side of one implicit-Euler step (Sec. 1.2): b = c0 u_prev + h^alpha f.
- * f may be NULL (f = 0).  Device FP64 arrays of n1*n2 elements.
+ * Right-hand side of one time step, per the plan's scheme:
+ *   implicit Euler (Sec. 1.2):    b = c0 u_prev + h^alpha f        (c0 = h^alpha / dt)
+ *   Crank-Nicolson (Sec. 1.4):    b = (2 c0 I - M) u_prev + 2 h^alpha f
+ *                                 (c0 = 1/r = 2 h^alpha / dt; f at the half step),
+ * the explicit operator applied with the plan's FP64 matvec.  f may be NULL
+ * (f = 0).  Device FP64 arrays of n1*n2 elements; u_prev != b.
  */
 fde_status fde_step_rhs(const fde_plan* plan, const double* u_prev, const double* f,
                         double* b, void* stream);

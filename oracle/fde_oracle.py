@@ -44,13 +44,14 @@ __all__ = [
     "symbol_g", "symbol_w", "symbol_p", "symbol_q", "scheme_symbol", "tau_grid",
     "sine_matrix", "tau_matrix", "Problem1D", "Problem2D", "Tau1D", "Tau2D",
     "pcg", "gmres", "KrylovResult", "preconditioned_condition_number",
-    "apply_sine_fast", "ORDER_TAU_D", "ORDER_D_TAU", "GL1", "WSGD2",
+    "apply_sine_fast", "ORDER_TAU_D", "ORDER_D_TAU", "ORDER_TAU_DF", "GL1", "WSGD2",
 ]
 
 GL1 = "gl1"      # first-order shifted Grunwald weights g_k (Sec. 1.2)
 WSGD2 = "wsgd2"  # second-order weighted-and-shifted weights w_k (Sec. 1.3)
 ORDER_TAU_D = "tau_d"   # P = tau(F) D   (reproduces Tables 1-4)
 ORDER_D_TAU = "d_tau"   # P = D tau(F)   (as printed in Sec. 3.1 / 3.2)
+ORDER_TAU_DF = "tau_df" # P = S diag(D_j F(theta_j)) S: P_F-tilde of Table 2 (1D)
 
 
 # ----------------------------------------------------------------------------
@@ -332,6 +333,10 @@ class Tau1D:
         D = 0.5 * (prob.dp + prob.dm)
         if shift:
             F = F + prob.c0 / float(np.mean(D))
+        if order == ORDER_TAU_DF:
+            # P_F-tilde (Sec. 4, Table 2): D_n sampled on the tau grid and folded
+            # into the symbol, P = S diag(D_j F_j) S, no separate D
+            return Tau1D(F=D * F, D=None, order=ORDER_TAU_D)
         return Tau1D(F=F, D=D, order=order)
 
     def tau_inv(self, r: np.ndarray) -> np.ndarray:

@@ -94,7 +94,8 @@ fde_status validate(const fde_problem* p, const fde_solve_opts* o) {
     if (!(p->len1 > 0.0) || !std::isfinite(p->len1) || !(p->dt > 0.0) || !std::isfinite(p->dt)) return FDE_EINVAL;
     if (p->scheme != FDE_SCHEME_IMPLICIT_EULER && p->scheme != FDE_SCHEME_CRANK_NICOLSON) return FDE_EINVAL;
     if (p->weights != FDE_WEIGHTS_GL1 && p->weights != FDE_WEIGHTS_WSGD2) return FDE_EINVAL;
-    if (p->order != FDE_ORDER_TAU_D && p->order != FDE_ORDER_D_TAU) return FDE_EINVAL;
+    if (p->order != FDE_ORDER_TAU_D && p->order != FDE_ORDER_D_TAU && p->order != FDE_ORDER_TAU_DF) return FDE_EINVAL;
+    if (p->order == FDE_ORDER_TAU_DF && (p->dim != 1 || p->tau_shift)) return FDE_EINVAL;   // P_F-tilde: 1D
     if (p->tau_shift != 0 && p->tau_shift != 1) return FDE_EINVAL;
     if (!coeff_ok(p->dp, p->dp_const) || !coeff_ok(p->dm, p->dm_const)) return FDE_EINVAL;
     if (p->dim == 2) {
@@ -143,7 +144,10 @@ struct Layout {
 };
 
 // D^{-1} is applied unless the shifted symbol absorbs a constant D (Case I, P_hat).
-bool compute_has_D(const fde_problem* p) { return !p->tau_shift || (p->dim == 1 && (p->dp || p->dm)); }
+bool compute_has_D(const fde_problem* p) {
+    if (p->order == FDE_ORDER_TAU_DF) return false;      // D folded into the symbol
+    return !p->tau_shift || (p->dim == 1 && (p->dp || p->dm));
+}
 
 Layout layout(const fde_problem* p, const fde_solve_opts* o) {
     Layout L{};
@@ -207,6 +211,9 @@ struct AxisJob {
     int kind;              // 0: 1D tau multiplier 1/(L (add + mult F)); 1: 2D axis part add + mult F
     double add, mult;
     const double* dbar;    // kind 0 with a variable D: multiplier 1/(L (F + add / dbar))
+    int fold_d;            // kind 0, P_F-tilde: multiplier 1/(L D_j F_j), D_j = (d_+ + d_-)/2 at x_j
+    const double *dp, *dm;
+    double dpc, dmc;
     const cx<double>* tw64;
     cx<double>* lam64;
     cx<float>* lam32;
@@ -271,8 +278,14 @@ __global__ void __launch_bounds__(1024) k_axis(AxisJob J) {
         double v = 0.0;
         if (j >= 1 && j <= n) {
             const double F = symbol_sample(J.alpha, J.weights, j, Np);
-            if (J.kind == 0 && J.dbar) v = invL / (F + J.add / *J.dbar);
-            else v = J.kind == 0 ? invL / (J.add + J.mult * F) : J.add + J.mult * F;
+            if (J.kind == 0 && J.dbar) {
+                v = invL / (F + J.add / *J.dbar);
+            } else if (J.kind == 0 && J.fold_d) {
+                const double Dj = 0.5 * ((J.dp ? J.dp[j - 1] : J.dpc) + (J.dm ? J.dm[j - 1] : J.dmc));
+                v = invL / (Dj * F);
+            } else {
+                v = J.kind == 0 ? invL / (J.add + J.mult * F) : J.add + J.mult * F;
+            }
         }
         J.phi64[j] = v;
         J.phi32[j] = (float)v;
@@ -332,9 +345,10 @@ __global__ void __launch_bounds__(1024) k_mean_d(long long N, const double* dp, 
 
 __global__ void k_write_inst(Inst v, Inst* dst) { *dst = v; }
 
-__global__ void k_step_rhs(long long N, double c0, double ha, const double* u, const double* f, double* b) {
+// b = a u + c f (f may be null).
+__global__ void k_step_rhs(long long N, double a, double c, const double* u, const double* f, double* b) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        b[i] = c0 * u[i] + (f ? ha * f[i] : 0.0);
+        b[i] = a * u[i] + (f ? c * f[i] : 0.0);
 }
 
 // Team sizes for one batched solve: instance i gets a share of the G CTAs in
@@ -576,6 +590,13 @@ fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* op
             J.kind = 0;
             J.add = shift ? I.c0 : 0.0;
             J.mult = shift ? dbar : 1.0;
+            if (prob->order == FDE_ORDER_TAU_DF) {
+                J.fold_d = 1;
+                J.dp = prob->dp;
+                J.dm = prob->dm;
+                J.dpc = prob->dp_const;
+                J.dmc = prob->dm_const;
+            }
             if (shift && (prob->dp || prob->dm)) {
                 double* dbar_dev = at<double>(workspace, Lo.dbar);
                 k_mean_d<<<1, 1024, 0, st>>>(I.N, prob->dp, prob->dm, prob->dp_const, prob->dm_const, dbar_dev);
@@ -769,11 +790,17 @@ fde_status fde_krylov_solve(const fde_plan* const* plans, int count, const doubl
 
 fde_status fde_step_rhs(const fde_plan* p, const double* u_prev, const double* f, double* b, void* stream) {
     if (!p || !u_prev || !b || u_prev == b) return FDE_EINVAL;
-    if (p->prob.scheme != FDE_SCHEME_IMPLICIT_EULER) return FDE_EINVAL;
     const long long N = p->inst.N;
     const int blocks = (int)std::min<long long>(4096, (N + 255) / 256);
-    k_step_rhs<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(N, p->inst.c0, p->inst.h_alpha, u_prev, f, b);
-    return cudaGetLastError() == cudaSuccess ? FDE_OK : FDE_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (p->prob.scheme == FDE_SCHEME_IMPLICIT_EULER) {
+        k_step_rhs<<<blocks, 256, 0, st>>>(N, p->inst.c0, p->inst.h_alpha, u_prev, f, b);
+        return cudaGetLastError() == cudaSuccess ? FDE_OK : FDE_ECUDA;
+    }
+    // Crank-Nicolson: the explicit half, b = (2 c0 I - M) u_prev + 2 h^alpha f
+    k_step_rhs<<<blocks, 256, 0, st>>>(N, 2.0 * p->inst.c0, 2.0 * p->inst.h_alpha, u_prev, f, b);
+    if (cudaGetLastError() != cudaSuccess) return FDE_ECUDA;
+    return launch_op(p, kOpMatvecSub, FDE_F64, u_prev, b, stream);
 }
 
 }  // extern "C"

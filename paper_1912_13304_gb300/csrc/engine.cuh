@@ -8,7 +8,7 @@
 
 namespace fde {
 
-enum Op : int { kOpSolve = 0, kOpMatvec = 1, kOpTau = 2 };
+enum Op : int { kOpSolve = 0, kOpMatvec = 1, kOpTau = 2, kOpMatvecSub = 3 };   // kOpMatvecSub: out -= M in
 enum Mode : int { kModeF64 = 0, kModeF32 = 1, kModeIR = 2 };
 
 struct EngineArgs {
@@ -130,6 +130,8 @@ FDE_D bool run_op(const Team& t, const Inst& I, const EngineArgs& a, int idx, co
         const double* in = reinterpret_cast<const double*>(a.in[idx]);
         double* out = reinterpret_cast<double*>(a.out[idx]);
         if (a.op == kOpMatvec) return op_matvec<double>(t, I, lm_f64(I), in, 1.0, out, I.t64, wk);
+        if (a.op == kOpMatvecSub)
+            return op_matvec_out<double>(t, I, lm_f64(I), in, 1.0, I.t64, OutSpec<double>{kOutResid, out, out}, wk);
         return op_tau<double>(t, I, lm_f64(I), in, 1.0, out, wk);
     }
     if constexpr (MODE != kModeF64) {
@@ -137,6 +139,8 @@ FDE_D bool run_op(const Team& t, const Inst& I, const EngineArgs& a, int idx, co
         float* out = reinterpret_cast<float*>(a.out[idx]);
         float* tmp = reinterpret_cast<float*>(I.t64);
         if (a.op == kOpMatvec) return op_matvec<float>(t, I, lm_f32(I), in, 1.0f, out, tmp, wk);
+        if (a.op == kOpMatvecSub)
+            return op_matvec_out<float>(t, I, lm_f32(I), in, 1.0f, tmp, OutSpec<float>{kOutResid, out, out}, wk);
         return op_tau<float>(t, I, lm_f32(I), in, 1.0f, out, wk);
     }
     return true;

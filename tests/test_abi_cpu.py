@@ -53,7 +53,7 @@ def test_workspace_size_valid_problems(L):
 
 @pytest.mark.parametrize("field,value", [
     ("n1", 0), ("n1", 1000), ("alpha", 1.0), ("alpha", 2.0), ("alpha", float("nan")), ("dt", 0.0),
-    ("len1", -1.0), ("dim", 3), ("weights", 5), ("order", 2), ("scheme", 7),
+    ("len1", -1.0), ("dim", 3), ("weights", 5), ("order", 3), ("scheme", 7),
 ])
 def test_invalid_problem_rejected(L, field, value):
     o = fde.make_opts()
@@ -71,6 +71,16 @@ def test_invalid_opts_rejected(L, field, value):
     o = fde.make_opts()
     setattr(o, field, value)
     st, _ = _ws(fde.make_problem(1, 255, 1.5, 0.01), o)
+    assert st == fde.EINVAL
+
+
+def test_ftilde_order_is_1d_and_unshifted(L):
+    o = fde.make_opts()
+    st, _ = _ws(fde.make_problem(1, 255, 1.5, 0.01, dp=1 << 20, dm=1 << 20, order="tau_df"), o)
+    assert st == fde.OK
+    st, _ = _ws(fde.make_problem(2, 63, 1.5, 0.01, n2=63, beta=1.5, order="tau_df"), o)
+    assert st == fde.EINVAL
+    st, _ = _ws(fde.make_problem(1, 255, 1.5, 0.01, order="tau_df", tau_shift=True), o)
     assert st == fde.EINVAL
 
 

@@ -89,6 +89,17 @@ def test_tau_1d(gpu, n, variant, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("n", [1, 7, 63, 1023, 4095, 16383, 65535])
+def test_tau_1d_ftilde(gpu, n, dtype):
+    # P_F-tilde (Table 2): D_j folded into the symbol samples
+    plan, prob = make_1d(gpu, n, "var", order="tau_df")
+    P = oracle.Tau1D.for_problem(prob, order="tau_df")
+    r = np.random.default_rng(n + 9).uniform(-1, 1, n)
+    z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
+    assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("order", ["tau_d", "d_tau"])
 @pytest.mark.parametrize("n", [7, 1023, 4095, 16383, 65535])
 def test_tau_1d_shifted_variable_coefficients(gpu, n, order, dtype):

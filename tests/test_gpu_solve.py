@@ -387,3 +387,74 @@ def test_autotuned_schedule_full_size_and_2d(gpu):
     assert info["status"] == fde.OK, info
     x = info["x"].cpu().numpy()
     assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_step_rhs_crank_nicolson(gpu, dim):
+    # b = (2 c0 I - M) u + 2 h^alpha f (Sec. 1.4) against the oracle's matvec
+    rng = np.random.default_rng(21 + dim)
+    if dim == 1:
+        n, alpha, dt = 1023, 1.6, 1.0 / 64
+        h = 1.0 / (n + 1)
+        xg = h * np.arange(1, n + 1)
+        dp, dm = 1 + xg, 2 - xg
+        plan = fde.Plan(1, n, alpha, dt, scheme="cn", dp=dp, dm=dm)
+        prob = oracle.Problem1D(alpha=alpha, n=n, c0=2 * h ** alpha / dt, dp=dp, dm=dm)
+        N, ha = n, h ** alpha
+    else:
+        from oracle.examples import example2_problem
+        prob, meta = example2_problem(1.4, 1.7, 63)
+        plan = fde.Plan(2, 63, 1.4, meta["ht"], n2=63, beta=1.7, len1=2.0, len2=2.0, scheme="cn", weights="wsgd2",
+                        dp=prob.dp, dm=prob.dm, ep=prob.ep, em=prob.em)
+        N, ha = 63 * 63, meta["h"] ** 1.4
+    u = rng.uniform(-1, 1, N)
+    f = rng.uniform(-1, 1, N)
+    b = plan.rhs(to_dev(gpu, u, "f64"), f=to_dev(gpu, f, "f64")).cpu().numpy()
+    assert abs(plan.c0 - prob.c0) <= 1e-14 * prob.c0
+    ref = 2 * prob.c0 * u - prob.matvec(u) + 2 * ha * f
+    scale = np.max(np.abs(2 * prob.c0 * u)) + np.max(np.abs(prob.matvec(u)))
+    assert np.max(np.abs(b - ref)) / scale < 1e-12
+
+
+def test_crank_nicolson_example2_march_matches_oracle(gpu):
+    # Example 2 (Sec. 4.2): the whole Crank-Nicolson march in paper mode (left
+    # GMRES(20), tol 1e-7, tau(F) D), right-hand sides built on the device
+    from oracle.examples import example2_exact, example2_march, example2_problem, example2_source
+    alpha, beta, n = 1.5, 1.5, 31          # n + 1 = 2^k (the library's grids); 31 steps
+    u_ref, its_ref, exact = example2_march(alpha, beta, n)
+    prob, meta = example2_problem(alpha, beta, n)
+    X, Y, h, ht = meta["X"], meta["Y"], meta["h"], meta["ht"]
+    plan = fde.Plan(2, n, alpha, ht, n2=n, beta=beta, len1=2.0, len2=2.0, scheme="cn", weights="wsgd2",
+                    dp=prob.dp, dm=prob.dm, ep=prob.ep, em=prob.em, restart=20)
+    u = to_dev(gpu, example2_exact(X, Y, 0.0).reshape(-1), "f64")
+    its = []
+    for m in range(1, meta["steps"] + 1):
+        f = to_dev(gpu, example2_source(alpha, beta, X, Y, (m - 0.5) * ht).reshape(-1), "f64")
+        b = plan.rhs(u, f=f)
+        info = plan.solve(b, tol=1e-7, side="left")
+        assert info["status"] == fde.OK, (m, info)
+        u = info["x"]
+        its.append(info["iterations"])
+    assert all(abs(a - r) <= 1 for a, r in zip(its, its_ref)), (its, its_ref)
+    ug = u.cpu().numpy()
+    assert rel_err(ug, u_ref) < 1e-6
+    # and the discretisation error is the oracle's (the paper's O(h^2) scheme)
+    assert abs(np.max(np.abs(ug - exact)) - np.max(np.abs(u_ref - exact))) < 1e-6 * np.max(np.abs(exact))
+
+
+@pytest.mark.parametrize("n", [63, 255])
+def test_gmres_left_ftilde_example1(gpu, n):
+    """P_F-tilde (Sec. 4, Table 2) in paper mode on Example 1."""
+    from oracle.examples import example1_exact, example1_problem, example1_source
+    prob, meta = example1_problem(1.5, n)
+    x = meta["x"]
+    plan = fde.Plan(1, n, 1.5, meta["ht"], len1=2.0, dp=prob.dp, dm=prob.dm, restart=20, order="tau_df")
+    P = oracle.Tau1D.for_problem(prob, order="tau_df")
+    u = example1_exact(x, 0.0)
+    for m in range(1, 4):
+        b = prob.c0 * u + meta["h"] ** 1.5 * example1_source(1.5, x, m * meta["ht"])
+        ref = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, side="left", restart=20, tol=1e-7)
+        info = plan.solve(to_dev(gpu, b, "f64"), tol=1e-7, side="left")
+        assert abs(info["iterations"] - ref.iterations) <= 1, (m, info, ref.iterations)
+        assert rel_err(info["x"].cpu().numpy(), ref.x) < 1e-6
+        u = ref.x

@@ -277,6 +277,17 @@ def test_table2_alternative_symbol_condition_numbers(golden, alpha):
         assert round(preconditioned_condition_number(prob.dense(), Pt), 1) == t["PFtilde_kappa"][alpha][col]
 
 
+def test_tau1d_ftilde_reproduces_table2(golden):
+    """Tau1D's P_F-tilde order reproduces Table 2's printed condition numbers."""
+    t = golden["table2_example1"]
+    for alpha in t["PFtilde_kappa"]:
+        for col in (0, 1):
+            n = t["n_plus_1"][col] - 1
+            prob, _ = example1_problem(float(alpha), n)
+            P = Tau1D.for_problem(prob, order="tau_df").dense()
+            assert round(preconditioned_condition_number(prob.dense(), P), 1) == t["PFtilde_kappa"][alpha][col]
+
+
 def test_printed_D_tau_order_does_not_reproduce_table1(golden):
     """The formula order P = D tau(F) gives 30.9 where Table 1 prints 30.8."""
     prob, _ = example1_problem(1.2, 63)
