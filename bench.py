@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--graph", type=int, default=1, help="1: replay the time-step loop as a CUDA graph")
     ap.add_argument("--batch", type=int, default=1, help="1: also time the 256-instance batched workload")
     ap.add_argument("--two-d", type=int, default=1, help="1: also time the two 2D workloads")
+    ap.add_argument("--only", default="", choices=["", "2d", "batch"],
+                    help="time only this section and print its results (for profiling one kernel)")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: pick each plan's transform schedule with fde_autotune before timing")
     ap.add_argument("--variants", type=int, default=1,
@@ -484,6 +486,11 @@ def main():
         torch.distributed.init_process_group("nccl")
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    if args.only:
+        out = run_2d(args, device) if args.only == "2d" else run_batch(args, device)
+        if rank == 0:
+            print(json.dumps({"section": args.only, "results": out}), flush=True)
+        return
     res = run_ours(args, rank, world, device)
     batch = run_batch(args, device) if args.batch else None
     two_d = run_2d(args, device) if args.two_d else None

@@ -182,10 +182,11 @@ FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, 
 // one radix item per thread (registers hold RAD values), so a call requires
 // nlines * P / RAD <= kFftItems<R> * blockDim.x for the smallest radix it uses.
 //
-// Radix items per thread and pass: two for FP32 (twice the butterflies
-// between two barriers, registers to spare), one for FP64 (whose 8-point
-// butterfly already holds 32 registers).
-template <typename R> constexpr int kFftItems = sizeof(R) == 4 ? 2 : 1;
+// Radix items per thread and pass.  One: two items per thread (measured for
+// FP32 with 512 threads, and for both precisions with 256 threads and twice
+// the registers) raised the register saves of every phase function and was
+// slower overall.
+template <typename R> constexpr int kFftItems = 1;
 
 template <typename R, bool INV>
 FDE_D void fft_inplace(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
@@ -210,7 +211,7 @@ FDE_HD int fft_items_per_line(int logP) {
     return logP >= last ? 1 << (logP - last) : 1;
 }
 FDE_HD int fft_lines_per_call(int logP, int threads, int elem_bytes) {
-    return threads * (elem_bytes == 4 ? 2 : 1) / fft_items_per_line(logP);
+    return threads * (elem_bytes == 4 ? kFftItems<float> : kFftItems<double>) / fft_items_per_line(logP);
 }
 
 // FFT of nlines lines of 2^logP at stride lstride (flat index), in batches
