@@ -202,15 +202,17 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
         const size_t hdr = kshared_bytes(m, s_inst.logTsm);
         KShared ks = kshared_carve(dsm, m);
         ks.wide = reinterpret_cast<double*>(dsm + hdr);
-        // quarter-wave twiddle table of W_T, T = 2^logTsm, from the global table
+        // quarter-wave twiddle table of W_T, T = 2^logTsm, from the global table;
+        // entry i at pad(i), so the strided lookups of the later radix passes
+        // (index r k 2^s) spread over the banks
         {
             const int q = (1 << s_inst.logTsm) >> 2;
             const int sh = s_inst.logTW - s_inst.logTsm;
-            ks.twq32 = reinterpret_cast<cx<float>*>(ks.twq + q);
+            ks.twq32 = reinterpret_cast<cx<float>*>(ks.twq + padded_len(q));
             for (int i = threadIdx.x; i < q; i += blockDim.x) {
                 const cx<double> w = s_inst.tw64[i << sh];
-                ks.twq[i] = w;
-                ks.twq32[i] = mk((float)w.x, (float)w.y);
+                ks.twq[pad(i)] = w;
+                ks.twq32[pad(i)] = mk((float)w.x, (float)w.y);
             }
         }
         __syncthreads();

@@ -23,7 +23,7 @@ FDE_HD int padded_len(int n) { return n + (n >> 4) + 1; }
 
 // Twiddle sources of one CTA.
 struct Tw {
-    const cx<double>* q;       // shared memory: W_T^t for t < T/4 (quarter wave)
+    const cx<double>* q;       // shared memory: W_T^t for t < T/4 (quarter wave), entry t at pad(t)
     const cx<float>* q32;      // the same table rounded to FP32
     int logT;
     const cx<double>* g64;     // global: W_TW^t for t < TW
@@ -37,8 +37,8 @@ template <> FDE_D const cx<float>* tw_global_table<float>(const Tw& t) { return 
 
 // W_T^idx (idx < T) from the quarter table: W^{q T/4 + r} = (-i)^q W^r.
 template <typename R> FDE_D cx<R> tw_quarter_entry(const Tw& t, int r);
-template <> FDE_D cx<double> tw_quarter_entry<double>(const Tw& t, int r) { return t.q[r]; }
-template <> FDE_D cx<float> tw_quarter_entry<float>(const Tw& t, int r) { return t.q32[r]; }
+template <> FDE_D cx<double> tw_quarter_entry<double>(const Tw& t, int r) { return t.q[pad(r)]; }
+template <> FDE_D cx<float> tw_quarter_entry<float>(const Tw& t, int r) { return t.q32[pad(r)]; }
 
 // Sign flip by an integer XOR of the sign bit (flip = 0 or 1), which keeps
 // the selection off the floating-point pipes.

@@ -73,7 +73,8 @@ FDE_HD size_t kshared_scalar_bytes(int m) {
 // Rounded to 256 bytes: the transform buffers that follow need 16-byte
 // alignment whatever the table size.
 FDE_HD size_t kshared_bytes(int m, int logT) {
-    const size_t b = kshared_scalar_bytes(m) + (((size_t)1 << logT) / 4) * (sizeof(cx<double>) + sizeof(cx<float>));
+    // the quarter-wave tables are padded like the line buffers (entry i at pad(i))
+    const size_t b = kshared_scalar_bytes(m) + (size_t)padded_len((1 << logT) / 4) * (sizeof(cx<double>) + sizeof(cx<float>));
     return (b + 255) & ~(size_t)255;
 }
 
