@@ -99,6 +99,13 @@ FDE_D KShared kshared_carve(unsigned char* base, int m) {
 
 FDE_D bool finite(double v) { return isfinite(v); }
 
+// sum_{q < n} v_q^2 by one thread with four interleaved accumulators (fixed order).
+FDE_D double sum_squares(const double* v, int n) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < n; ++q) a[q & 3] += v[q] * v[q];
+    return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
 // ---------------------------------------------------------------------------
 // Reductions over N-vectors
 // ---------------------------------------------------------------------------
@@ -443,6 +450,7 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
             if (j > 0) {
                 // V_j = w - sum_q coef_q V_q, streamed once; the transforms then
                 // read a plain vector
+                trace_mark(t, 24);
                 form_basis<W>(t, N, v.w, v.V, kcoef<W>(ks), ncoef, v.V + (long long)j * N);
                 if (!team_sync(t)) return false;
                 trace_mark(t, 25);
@@ -455,8 +463,7 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
             // the FP64 pipe.
             if (threadIdx.x == 0) {
                 const double ww = ks.red[j + 1];
-                double hh = 0.0;
-                for (int q = 0; q <= j; ++q) hh += ks.red[q] * ks.red[q];
+                const double hh = sum_squares(ks.red, j + 1);
                 // ||w - V h|| > ||w|| / sqrt(2) (the Daniel-Gragg-Kaufman-Stewart
                 // criterion): one classical Gram-Schmidt pass is enough
                 const bool once = hh < 0.5 * ww;
@@ -482,17 +489,15 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
                 __syncthreads();
                 form_basis<W>(t, N, v.w, v.V, kcoef<W>(ks), j + 1, v.w);
                 __syncthreads();
+                trace_mark(t, 32);
                 if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
                 trace_mark(t, 31);
-                if (threadIdx.x == 0) {
-                    double s2 = 0.0;
-                    for (int q = 0; q <= j; ++q) s2 += ks.red[q] * ks.red[q];
-                    ks.sc[1] = ks.red[j + 1] - s2;
-                    for (int q = 0; q <= j; ++q) {
-                        ks.H[q + j * (m + 1)] = ks.y[q] + ks.red[q];
-                        set_coef(ks, q, ks.red[q] * ks.vs[q]);
-                    }
+                if (threadIdx.x == 0) ks.sc[1] = ks.red[j + 1] - sum_squares(ks.red, j + 1);
+                if (threadIdx.x <= j) {
+                    ks.H[threadIdx.x + j * (m + 1)] = ks.y[threadIdx.x] + ks.red[threadIdx.x];
+                    set_coef(ks, threadIdx.x, ks.red[threadIdx.x] * ks.vs[threadIdx.x]);
                 }
+                __syncthreads();
             }
             ncoef = j + 1;
             if (threadIdx.x == 0) {

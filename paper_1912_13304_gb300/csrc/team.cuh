@@ -97,8 +97,12 @@ FDE_D void block_sum(const double (&v)[K], double* out, double* wide) {
     for (int k = 0; k < K; ++k) wide[k * nt + threadIdx.x] = v[k];
     __syncthreads();
     if (warp < K) {
-        double s = 0.0;
-        for (int i = lane; i < nt; i += 32) s += wide[warp * nt + i];
+        // four interleaved partial sums, then a fixed tree: short dependency
+        // chains (a dependent FP64 add is slow here), still one fixed order
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        int u = 0;
+        for (int i = lane; i < nt; i += 32, u = (u + 1) & 3) a[u] += wide[warp * nt + i];
+        double s = (a[0] + a[1]) + (a[2] + a[3]);
         s = warp_sum(s);
         if (lane == 0) out[warp] = s;
     }
