@@ -241,6 +241,16 @@ fde_status fde_plan_set_schedule(fde_plan* plan, int ctas, int log_p1, void* str
  */
 fde_status fde_autotune(fde_plan* plan, void* stream, int* ctas, int* log_p1);
 
+/*
+ * Failure-path self-test (no counterpart in the paper): one CTA enters a
+ * two-CTA team barrier on the plan's sync area with a bound of 2e6 clock
+ * cycles (about 1 ms); the second member is never launched.  The bounded wait
+ * must run out and report it: *status_dev (device int) receives FDE_ETIMEOUT,
+ * the same status a solve reports when a team member stops arriving.  The
+ * sync area is cleared before and after.  Asynchronous on `stream`.
+ */
+fde_status fde_selftest_barrier_timeout(const fde_plan* plan, int* status_dev, void* stream);
+
 /* Scalars the plan derived from the problem: c0, sr, h1^alpha. */
 fde_status fde_plan_scalars(const fde_plan* plan, double* c0, double* sr, double* h_alpha);
 

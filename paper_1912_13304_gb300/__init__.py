@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
         L.fde_assemble_symbol.restype = cint
         L.fde_toeplitz_matvec.argtypes = [vp, cint, vp, vp, vp]
         L.fde_toeplitz_matvec.restype = cint
+        L.fde_selftest_barrier_timeout.argtypes = [vp, vp, vp]
+        L.fde_selftest_barrier_timeout.restype = cint
         L.fde_plan_set_schedule.argtypes = [vp, cint, cint, vp]
         L.fde_plan_set_schedule.restype = cint
         L.fde_autotune.argtypes = [vp, vp, P(cint), P(cint)]

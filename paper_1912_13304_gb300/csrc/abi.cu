@@ -1167,3 +1167,38 @@ extern "C" fde_status fde_autotune(fde_plan* p, void* stream, int* ctas_out, int
     if (log_p1_out) *log_p1_out = pick.second;
     return FDE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Failure-path self-test: a team barrier whose partner never arrives
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// One CTA joins a team of two on the plan's sync area with a short wait
+// bound; the second member is never launched, so the wait runs out and the
+// barrier must report it (abort flag set, false returned) instead of hanging.
+__global__ void k_barrier_selftest(SyncArea* sync, long long bound, int* status) {
+    Team t;
+    t.rank = 0;
+    t.size = 2;
+    t.count = &sync->bar_count[0];
+    t.gen = &sync->bar_gen[0];
+    t.partial = sync->partial;
+    t.abort_flag = &sync->abort_flag;
+    t.sync = sync;
+    const bool ok = team_sync(t, bound);
+    if (threadIdx.x == 0) *status = ok ? FDE_OK : FDE_ETIMEOUT;
+}
+
+}  // namespace
+
+extern "C" fde_status fde_selftest_barrier_timeout(const fde_plan* p, int* status_dev, void* stream) {
+    if (!p || !status_dev) return FDE_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(p->sync_dev, 0, offsetof(SyncArea, partial), st) != cudaSuccess) return FDE_ECUDA;
+    k_barrier_selftest<<<1, kThreads, 0, st>>>(p->sync_dev, 2000000LL, status_dev);
+    if (cudaGetLastError() != cudaSuccess) return FDE_ECUDA;
+    // leave the sync area clean for the plan's next launch
+    if (cudaMemsetAsync(p->sync_dev, 0, offsetof(SyncArea, partial), st) != cudaSuccess) return FDE_ECUDA;
+    return FDE_OK;
+}

@@ -413,6 +413,11 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
         if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
     }
     const double nb = sqrt(ks.red[0]);
+    if (!finite(nb)) {  // NaN or Inf in the right-hand side
+        st.relres = st.relres_est = nb;
+        st.status = FDE_ENONFINITE;
+        return team_sync(t);
+    }
     if (!(nb > 0.0)) {  // zero right-hand side: x = 0 is exact
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sol[i] = W(0);
         st.relres = st.relres_est = 0.0;
@@ -558,7 +563,12 @@ FDE_NI bool gmres_left_core(const Team& t, const Inst& I, int lm, const W* rhs, 
         if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
     }
     const double nb = sqrt(ks.red[0]);
-    if (!(nb > 0.0)) {
+    if (!finite(nb)) {  // NaN or Inf in the right-hand side
+        st.relres = st.relres_est = nb;
+        st.status = FDE_ENONFINITE;
+        return team_sync(t);
+    }
+    if (!(nb > 0.0)) {  // zero right-hand side: x = 0 is exact
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sol[i] = W(0);
         st.relres = st.relres_est = 0.0;
         st.status = FDE_OK;
@@ -683,7 +693,12 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
         if (!dots_pairs<W, 1>(t, N, a, a, ks)) return false;
     }
     const double nb = sqrt(ks.red[0]);
-    if (!(nb > 0.0)) {
+    if (!finite(nb)) {  // NaN or Inf in the right-hand side
+        st.relres = st.relres_est = nb;
+        st.status = FDE_ENONFINITE;
+        return team_sync(t);
+    }
+    if (!(nb > 0.0)) {  // zero right-hand side: x = 0 is exact
         for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) sol[i] = W(0);
         st.relres = st.relres_est = 0.0;
         st.status = FDE_OK;

@@ -42,7 +42,7 @@ FDE_D unsigned int ld_volatile(const unsigned int* p) {
 }
 
 // Returns false when the launch is being aborted (a barrier timed out).
-FDE_D bool team_sync(const Team& t) {
+FDE_D bool team_sync(const Team& t, long long bound = kBarrierCycles) {
     __shared__ int s_ok;
     if (t.size == 1) {
         __syncthreads();
@@ -61,7 +61,7 @@ FDE_D bool team_sync(const Team& t) {
         } else {
             const long long t0 = clock64();
             while (ld_volatile(t.gen) == g) {
-                if (clock64() - t0 > kBarrierCycles) {
+                if (clock64() - t0 > bound) {
                     ok = 0;
                     atomicExch(t.abort_flag, 1u);
                     break;

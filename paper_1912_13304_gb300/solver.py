@@ -23,7 +23,7 @@ class Plan:
                  dp=None, dm=None, ep=None, em=None, dp_const: float = 1.0, dm_const: float = 1.0,
                  ep_const: float = 1.0, em_const: float = 1.0, tau_shift: bool = False,
                  order: str = "tau_d", method: str = "gmres", restart: int = 30, precision: str = "f64",
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, workspace_fill: Optional[int] = None):
         torch = _torch()
         self.device = torch.device(device)
         self._keep = []
@@ -50,6 +50,8 @@ class Plan:
         self.opts = make_opts(method=method, restart=restart, precision=precision)
         self.nbytes = workspace_size(self.problem, self.opts)
         self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+        if workspace_fill is not None:          # e.g. 0xFF: every double and float of it reads as NaN
+            self.workspace.fill_(workspace_fill)
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) & ~255
         self.handle = assemble_symbol(self.problem, self.opts, self._ws_ptr, self.nbytes, stream)
@@ -57,12 +59,14 @@ class Plan:
 
     @classmethod
     def from_workload(cls, w: dict, method: Optional[str] = None, precision: str = "f64", restart: Optional[int] = None,
-                      order: Optional[str] = None, shift: Optional[bool] = None, device="cuda", stream=None) -> "Plan":
+                      order: Optional[str] = None, shift: Optional[bool] = None, device="cuda", stream=None,
+                      workspace_fill: Optional[int] = None) -> "Plan":
         """Plan for one workload dict of ``workloads`` (coefficients as constants when they are)."""
         kw = dict(dim=w["dim"], n1=w["n1"], alpha=w["alpha"], dt=w["dt"], len1=w["length"], len2=w["length"],
                   weights=w["scheme"], tau_shift=w["shift"] if shift is None else shift,
                   order=w["order"] if order is None else order, method=method or w["method"],
-                  restart=restart or max(1, w["restart"]), precision=precision, device=device, stream=stream)
+                  restart=restart or max(1, w["restart"]), precision=precision, device=device, stream=stream,
+                  workspace_fill=workspace_fill)
         if w["dim"] == 2:
             kw.update(n2=w["n2"], beta=w["beta"])
         if w["const_coeffs"]:

@@ -125,3 +125,14 @@ def test_calls_reject_null_arguments_without_launching(L):
     p = fde.make_problem(1, 255, 1.5, 0.01)
     assert L.fde_assemble_symbol(ctypes.byref(p), ctypes.byref(o), None, 0, ctypes.byref(h), None) == fde.EINVAL
     assert L.fde_step_rhs(None, None, None, None, None) == fde.EINVAL
+
+
+def test_assembly_rejects_a_short_workspace_before_any_launch(L):
+    p = fde.make_problem(1, 1023, 1.5, 0.01)
+    o = fde.make_opts()
+    st, need = _ws(p, o)
+    assert st == fde.OK
+    plan = ctypes.c_void_p()
+    # a 256-byte aligned address that is never dereferenced: the size check comes first
+    st = L.fde_assemble_symbol(ctypes.byref(p), ctypes.byref(o), 1 << 20, need - 1, ctypes.byref(plan), 0)
+    assert st == fde.ENOMEM and not plan.value
