@@ -182,7 +182,10 @@ Layout layout(const fde_problem* p, const fde_solve_opts* o) {
     const size_t wsz = o->precision == FDE_PREC_F64 ? sizeof(double) : sizeof(float);
     const long long nvec = o->method == FDE_GMRES ? (o->restart + 4) : 5;
     const long long extra = o->precision == FDE_PREC_F64 ? 0 : 2;
-    L.wvec = take((size_t)(nvec + extra) * N * wsz);
+    size_t wbytes = (size_t)(nvec + extra) * N * wsz;
+    // refinement plans may finish a solve in FP64 (the same vectors at FP64 size)
+    if (o->precision == FDE_PREC_F32_IR) wbytes = std::max<size_t>(wbytes, (size_t)nvec * (size_t)N * sizeof(double));
+    L.wvec = take(wbytes);
     const int npmax = std::max(L.Np[0], L.Np[1]);
     L.split64 = take((size_t)2 * npmax * sizeof(cx<double>));
     L.split32 = take((size_t)2 * npmax * sizeof(cx<float>));

@@ -81,6 +81,7 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
         } else {
             int status = FDE_ENOCONV;
             int inner_status = FDE_OK;
+            double rn_prev = 0.0;
             while (true) {
                 double rn;
                 if (!residual64(t, I, b, x, ks, wk, rn)) return false;
@@ -89,6 +90,22 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
                 if (rn <= a.tol * nb) { status = FDE_OK; break; }
                 if (outer >= a.max_outer || st.iterations >= a.max_iters) { status = FDE_ENOCONV; break; }
                 if (inner_status == FDE_EBREAKDOWN || inner_status == FDE_ENONFINITE) { status = inner_status; break; }
+                if (outer >= 1 && rn > 0.25 * rn_prev) {
+                    // A correction shrank the FP64 residual less than fourfold: the
+                    // FP32 operator does not resolve the error (kappa(M) u32 log2 L is
+                    // not small).  Finish this solve in FP64 from the current x.
+                    SolveState s64{};
+                    s64.iterations = st.iterations;
+                    SolveParams sp{a.tol, a.max_iters, a.side, 0};
+                    if (!krylov_core<double>(t, I, lm_f64(I), b, x, sp, s64, ks, wk)) return false;
+                    st.iterations = s64.iterations;
+                    st.restarts += s64.restarts;
+                    st.relres = s64.relres;
+                    st.relres_est = s64.relres_est;
+                    status = s64.status;
+                    break;
+                }
+                rn_prev = rn;
                 const double inv = 1.0 / rn;
                 for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
                     rhs32[i] = float(I.r64[i] * inv);

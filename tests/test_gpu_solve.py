@@ -458,3 +458,26 @@ def test_gmres_left_ftilde_example1(gpu, n):
         assert abs(info["iterations"] - ref.iterations) <= 1, (m, info, ref.iterations)
         assert rel_err(info["x"].cpu().numpy(), ref.x) < 1e-6
         u = ref.x
+
+
+@pytest.mark.parametrize("alpha", [1.2, 1.8])
+def test_refinement_switches_to_fp64_when_fp32_corrections_stall(gpu, alpha):
+    # alpha = 1.8 at n = 16383: kappa(M) u32 log2 L > 1, the FP32 corrections
+    # barely shrink the residual and the solve finishes in FP64 (close to the
+    # FP64 iteration count; FP32 refinement alone needed hundreds more).
+    # alpha = 1.2: the FP32 corrections contract and refinement continues.
+    n = 16383
+    w = workloads.config2(n=n, alphas=(alpha,))[0]
+    prob = oracle_problem_1d(w)
+    b = prob.c0 * w["u0"]
+    i64 = fde.Plan.from_workload(w).solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8)
+    pir = fde.Plan.from_workload(w, precision="f32_ir")
+    iir = pir.solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8, inner_tol=1e-3,
+                    max_iters=20000, max_outer=200)
+    assert iir["status"] == fde.OK and iir["relres"] <= 1e-8, iir
+    x = iir["x"].cpu().numpy()
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
+    if alpha == 1.8:
+        assert iir["iterations"] <= i64["iterations"] + 150, (iir, i64)
+    else:
+        assert iir["outer"] >= 2, iir
