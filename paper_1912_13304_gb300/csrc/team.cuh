@@ -41,6 +41,25 @@ FDE_D unsigned int ld_volatile(const unsigned int* p) {
     return *reinterpret_cast<const volatile unsigned int*>(p);
 }
 
+// GPU-scope acquire load, release add and acquire-release add (PTX memory
+// model): a CTA's writes before its arrival reach every CTA that observes the
+// barrier's release, without full fences.
+FDE_D unsigned int ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+FDE_D unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+FDE_D void atom_add_release_gpu(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    (void)old;
+}
+
 // Returns false when the launch is being aborted (a barrier timed out).
 FDE_D bool team_sync(const Team& t, long long bound = kBarrierCycles) {
     __shared__ int s_ok;
@@ -50,17 +69,19 @@ FDE_D bool team_sync(const Team& t, long long bound = kBarrierCycles) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // The CTA's writes precede this thread's release through the CTA
+        // barrier above (releases are cumulative).  Arrivals form a release
+        // sequence on the counter that the last arrival acquires; its release
+        // of the generation is acquired by every waiting CTA.
         int ok = 1;
-        const unsigned int g = ld_volatile(t.gen);
-        __threadfence();
-        const unsigned int arrived = atomicAdd(t.count, 1u);
+        const unsigned int g = ld_acquire_gpu(t.gen);
+        const unsigned int arrived = atom_add_acq_rel_gpu(t.count, 1u);
         if (arrived == (unsigned int)t.size - 1u) {
             atomicExch(t.count, 0u);
-            __threadfence();
-            atomicAdd(t.gen, 1u);
+            atom_add_release_gpu(t.gen, 1u);
         } else {
             const long long t0 = clock64();
-            while (ld_volatile(t.gen) == g) {
+            while (ld_acquire_gpu(t.gen) == g) {
                 if (clock64() - t0 > bound) {
                     ok = 0;
                     atomicExch(t.abort_flag, 1u);
@@ -68,8 +89,7 @@ FDE_D bool team_sync(const Team& t, long long bound = kBarrierCycles) {
                 }
             }
         }
-        __threadfence();
-        s_ok = ok && (ld_volatile(t.abort_flag) == 0u);
+        s_ok = ok && (ld_acquire_gpu(t.abort_flag) == 0u);
     }
     __syncthreads();
     return s_ok != 0;
