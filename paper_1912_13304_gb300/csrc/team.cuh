@@ -37,10 +37,6 @@ FDE_D void trace_mark(const Team& t, int code) {
 #endif
 }
 
-FDE_D unsigned int ld_volatile(const unsigned int* p) {
-    return *reinterpret_cast<const volatile unsigned int*>(p);
-}
-
 // GPU-scope acquire load, release add and acquire-release add (PTX memory
 // model): a CTA's writes before its arrival reach every CTA that observes the
 // barrier's release, without full fences.
