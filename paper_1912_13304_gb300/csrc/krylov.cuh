@@ -318,9 +318,10 @@ FDE_NI bool arnoldi_right(const Team& t, const Inst& I, int lm, Combo<W> u, int 
         trace_mark(t, 12);
         split_inv_cols<W>(t, I, wk, Y, Y2, cc, !sym, epi_mvx<W>(I, z, W(1), out_store<W>(w)));
         trace_mark(t, 13);
-        const int units = A.P2 / cc;
+        const int units = split_units(A, cc);
         return dots_own<W>(t, N, w, V, ks.vs, nd, true, ks, [&](auto f) {
-            for (int un = t.rank; un < units; un += t.size) split_unit_elements(A, un * cc, cc, f);
+            for (int un = t.rank; un < units; un += t.size)
+                split_unit_elements(A, un * cc, split_width(A, un * cc, cc), f);
         });
     }
     // 2D plane: rows (first sine transform) | columns (tau) | rows (second sine

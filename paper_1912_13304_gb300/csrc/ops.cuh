@@ -245,17 +245,23 @@ FDE_NI void cta_matvec_1d(const Inst& I, const Wk& wk, const W* x, W s, Epi<W> e
 // {j1, P1 - j1} whose spectral pairs (j, Np - j) meet in one unit.
 // ---------------------------------------------------------------------------
 
+// Columns per unit: ceil(P2 / team size), so every CTA of the team takes one
+// unit when shared memory allows; the last unit may be narrower (split_width).
+// A power-of-two width left up to a third of a team idle in the column phases
+// whenever the team size did not divide P2 (93 CTAs on 256 columns: 64 units
+// of 4), and those phases run at the FP64 rate of the busiest CTA.
 template <typename W>
 FDE_D int split_cols_per_unit(const AxisData& A, int team_size, int bytes) {
-    const int cap_smem = max_lines<W>(A.P1, 2, bytes);
-    const int cap_fft = fft_lines_per_call(A.logP1, kThreads, (int)sizeof(W));
-    const int cap = cap_smem < cap_fft ? cap_smem : cap_fft;
-    int cc = 1;
-    while (cc * team_size < A.P2) cc *= 2;          // units <= team size when possible
-    if (cc > cap) cc = pow2_floor(cap);
+    const int cap = max_lines<W>(A.P1, 2, bytes);
+    int cc = (A.P2 + team_size - 1) / team_size;
+    if (cc > cap) cc = cap;
     if (cc > A.P2) cc = A.P2;
     return cc < 1 ? 1 : cc;
 }
+
+FDE_D int split_units(const AxisData& A, int cc) { return (A.P2 + cc - 1) / cc; }
+// Columns of the unit that starts at column m2b.
+FDE_D int split_width(const AxisData& A, int m2b, int cc) { return A.P2 - m2b < cc ? A.P2 - m2b : cc; }
 
 // Element positions p (0-based) whose outputs a column unit [m2b, m2b+cc)
 // produces: k = 2m, 2m+1 (1 <= k <= n), m = P2 m1 + m2, m1 < P1/2.
@@ -280,19 +286,20 @@ FDE_NI void split_fwd_cols(const Team& t, const Inst& I, const Wk& wk, Combo<W> 
     const int tsh = wk.tw.logTW - A.logNp;
     const cx<W>* g = tw_global_table<W>(wk.tw);
     auto get = [&](int k, bool d) { return u.get(k - 1, d); };
-    const int units = P2 / cc;
+    const int units = split_units(A, cc);
     for (int un = t.rank; un < units; un += t.size) {
         const int m2b = un * cc;
-        for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
-            const int c = idx % cc, m1 = idx / cc;
+        const int wu = split_width(A, m2b, cc);
+        for (int idx = threadIdx.x; idx < wu * P1; idx += blockDim.x) {
+            const int c = idx % wu, m1 = idx / wu;
             buf[pad(c * P1 + m1)] = pack_elem<W, EXT>(get, P2 * m1 + m2b + c, n, Np);
         }
         __syncthreads();
         trace_mark(t, 50);
-        fft_lines<W, false>(buf, A.logP1, cc, P1, wk.tw);
+        fft_lines<W, false>(buf, A.logP1, wu, P1, wk.tw);
         trace_mark(t, 51);
-        for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
-            const int c = idx % cc, j1 = idx / cc;
+        for (int idx = threadIdx.x; idx < wu * P1; idx += blockDim.x) {
+            const int c = idx % wu, j1 = idx / wu;
             const int m2 = m2b + c;
             Y[(long long)j1 * P2 + m2] = buf[pad(c * P1 + j1)] * g[(j1 * m2) << tsh];
         }
@@ -362,7 +369,8 @@ FDE_NI void split_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>
     }
 }
 
-// Inverse column transform of one unit into the buffer (both sets when two).
+// Inverse column transform of one unit of cc columns (its own width) into the
+// buffer (both sets when two).
 template <typename W>
 FDE_D void split_inv_unit_fft(const Inst& I, const Wk& wk, const cx<W>* Y, const cx<W>* Y2, int m2b, int cc,
                               bool two) {
@@ -384,22 +392,23 @@ FDE_NI void split_inv_cols(const Team& t, const Inst& I, const Wk& wk, const cx<
                            bool two, Epi<W> epi) {
     const AxisData& A = I.ax[0];
     const cx<W>* buf = reinterpret_cast<const cx<W>*>(wk.smem);
-    const int units = A.P2 / cc;
+    const int units = split_units(A, cc);
     for (int un = t.rank; un < units; un += t.size) {
         const int m2b = un * cc;
-        split_inv_unit_fft<W>(I, wk, Y, Y2, m2b, cc, two);
+        const int wu = split_width(A, m2b, cc);
+        split_inv_unit_fft<W>(I, wk, Y, Y2, m2b, wu, two);
         trace_mark(t, 57);
-        const int total = (A.P1 / 2) * cc * 2;
+        const int total = (A.P1 / 2) * wu * 2;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int m1 = idx / (2 * cc);
-            const int rem = idx - m1 * 2 * cc;
+            const int m1 = idx / (2 * wu);
+            const int rem = idx - m1 * 2 * wu;
             const int c = rem >> 1, e = rem & 1;
             const long long k = 2LL * (A.P2 * m1 + m2b + c) + e;
             if (k >= 1 && k <= A.n) {
                 const cx<W> q = buf[pad(c * A.P1 + m1)];
                 W vb = W(0);
                 if (two) {
-                    const cx<W> q2 = buf[pad((cc + c) * A.P1 + m1)];
+                    const cx<W> q2 = buf[pad((wu + c) * A.P1 + m1)];
                     vb = e ? q2.y : q2.x;
                 }
                 epi(k - 1, e ? q.y : q.x, vb);
@@ -420,14 +429,15 @@ FDE_NI void split_tau_inv_mv_fwd(const Team& t, const Inst& I, const Wk& wk, con
     cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const W* dinv = Prec<W>::dinv(I);
     const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;
-    const int units = P2 / cc;
+    const int units = split_units(A, cc);
     const int tsh = wk.tw.logTW - A.logNp;
     const cx<W>* g = tw_global_table<W>(wk.tw);
     for (int un = t.rank; un < units; un += t.size) {
         const int m2b = un * cc;
-        split_inv_unit_fft<W>(I, wk, Yt, nullptr, m2b, cc, false);
+        const int wu = split_width(A, m2b, cc);
+        split_inv_unit_fft<W>(I, wk, Yt, nullptr, m2b, wu, false);
         trace_mark(t, 53);
-        for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < wu * P1; idx += blockDim.x) {
             const int c = idx / P1, m1 = idx - c * P1;
             const long long m = (long long)P2 * m1 + m2b + c;
             const cx<W> q = buf[pad(idx)];
@@ -448,10 +458,10 @@ FDE_NI void split_tau_inv_mv_fwd(const Team& t, const Inst& I, const Wk& wk, con
         }
         __syncthreads();
         trace_mark(t, 54);
-        fft_lines<W, false>(buf, A.logP1, cc, P1, wk.tw);
+        fft_lines<W, false>(buf, A.logP1, wu, P1, wk.tw);
         trace_mark(t, 55);
-        for (int idx = threadIdx.x; idx < cc * P1; idx += blockDim.x) {
-            const int c = idx % cc, j1 = idx / cc;
+        for (int idx = threadIdx.x; idx < wu * P1; idx += blockDim.x) {
+            const int c = idx % wu, j1 = idx / wu;
             const int m2 = m2b + c;
             Ym[(long long)j1 * P2 + m2] = buf[pad(c * P1 + j1)] * g[(j1 * m2) << tsh];
         }
