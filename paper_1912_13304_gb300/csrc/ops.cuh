@@ -310,6 +310,21 @@ FDE_NI void split_fwd_cols(const Team& t, const Inst& I, const Wk& wk, Combo<W> 
 
 // Row phase: P2-point FFTs of rows {j1, P1-j1}, spectral step on the pairs
 // (j, Np-j), inverse FFTs, inverse twiddle; back to Y (and Y2).
+//
+// A CTA takes all of its row units (u = rank, rank + size, ...) in one batch
+// when shared memory allows: one load, one forward FFT call over every line,
+// one spectral step, one inverse call, one store.  A unit's 256-point lines
+// keep one or two warps busy, so unit after unit left the phase bound by the
+// latency of short FP64 dependency chains; the batch puts all of them in
+// flight together.  Slot b of a batch holds lines 2b, 2b+1 (the second unused
+// for units 0 and 1, which have one row) and, for two outputs, lines
+// 2B + 2b, 2B + 2b + 1.
+FDE_D void split_row_unit(int u, int P1, int rows[2], int& nrows) {
+    nrows = u < 2 ? 1 : 2;
+    rows[0] = u == 0 ? 0 : (u == 1 ? P1 / 2 : u - 1);
+    rows[1] = P1 - rows[0];
+}
+
 template <typename W>
 FDE_NI void split_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W> mu, cx<W>* Y, cx<W>* Y2) {
     trace_mark(t, 40);
@@ -320,31 +335,40 @@ FDE_NI void split_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>
     const bool two = mu.kind == kMulLam2;
     cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const int units = P1 / 2 + 1;
-    for (int u = t.rank; u < units; u += t.size) {
-        const int nrows = u < 2 ? 1 : 2;
-        int rows[2];
-        rows[0] = u == 0 ? 0 : (u == 1 ? P1 / 2 : u - 1);
-        rows[1] = P1 - rows[0];
-        for (int idx = threadIdx.x; idx < nrows * P2; idx += blockDim.x) {
-            const int sl = idx / P2, j2 = idx - sl * P2;
-            buf[pad(idx)] = ldw(Y + (long long)rows[sl] * P2 + j2);
+    const int mine = t.rank < units ? (units - 1 - t.rank) / t.size + 1 : 0;
+    int per = max_lines<W>(P2, 4, wk.bytes);      // units per batch: four lines each
+    if (per < 1) per = 1;
+    for (int b0 = 0; b0 < mine; b0 += per) {
+        const int B = mine - b0 < per ? mine - b0 : per;
+        const int o2 = 2 * B * P2;                  // second output set
+        for (int idx = threadIdx.x; idx < 2 * B * P2; idx += blockDim.x) {
+            const int l = idx / P2, j2 = idx - l * P2;
+            const int b = l >> 1, sl = l & 1;
+            int rows[2], nrows;
+            split_row_unit(t.rank + (b0 + b) * t.size, P1, rows, nrows);
+            buf[pad(idx)] = sl < nrows ? ldw(Y + (long long)rows[sl] * P2 + j2) : mk(W(0), W(0));
         }
         __syncthreads();
         trace_mark(t, 41);
-        fft_lines<W, false>(buf, A.logP2, nrows, P2, wk.tw);
+        fft_lines<W, false>(buf, A.logP2, 2 * B, P2, wk.tw);
         trace_mark(t, 42);
-        const int npairs = u == 0 ? P2 / 2 + 1 : (u == 1 ? P2 / 2 : P2);
-        const int o2 = nrows * P2;            // second output set
-        for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+        for (int idx = threadIdx.x; idx < B * P2; idx += blockDim.x) {
+            const int b = idx / P2, q = idx - b * P2;
+            const int u = t.rank + (b0 + b) * t.size;
+            const int npairs = u == 0 ? P2 / 2 + 1 : (u == 1 ? P2 / 2 : P2);
+            if (q >= npairs) continue;
+            int rows[2], nrows;
+            split_row_unit(u, P1, rows, nrows);
             const int j2 = q;
             const int sm = u >= 2 ? 1 : 0;
             const int j2m = u == 0 ? ((P2 - q) & (P2 - 1)) : P2 - 1 - q;
             const int j = rows[0] + P1 * j2;           // frequency of the first element
             const cx<W> wj = tw_L<W>(wk.tw, j, A.logNp + 1);
-            const int ia = j2, ib = sm * P2 + j2m;
-            cx<W> a, b, al, be, al2, be2;
-            unpack_pair(buf[pad(ia)], buf[pad(ib)], wj, a, b);
-            mu.apply(j, 0, a, b, al, be, al2, be2);
+            const int base = 2 * b * P2;
+            const int ia = base + j2, ib = base + sm * P2 + j2m;
+            cx<W> a, bb, al, be, al2, be2;
+            unpack_pair(buf[pad(ia)], buf[pad(ib)], wj, a, bb);
+            mu.apply(j, 0, a, bb, al, be, al2, be2);
             cx<W> Qj, Qm;
             repack_pair(al, be, wj, Qj, Qm);
             buf[pad(ia)] = Qj;
@@ -357,10 +381,14 @@ FDE_NI void split_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>
         }
         __syncthreads();
         trace_mark(t, 43);
-        fft_lines<W, true>(buf, A.logP2, two ? 2 * nrows : nrows, P2, wk.tw);
+        fft_lines<W, true>(buf, A.logP2, two ? 4 * B : 2 * B, P2, wk.tw);
         trace_mark(t, 44);
-        for (int idx = threadIdx.x; idx < nrows * P2; idx += blockDim.x) {
-            const int sl = idx / P2, m2 = idx - sl * P2;
+        for (int idx = threadIdx.x; idx < 2 * B * P2; idx += blockDim.x) {
+            const int l = idx / P2, m2 = idx - l * P2;
+            const int b = l >> 1, sl = l & 1;
+            int rows[2], nrows;
+            split_row_unit(t.rank + (b0 + b) * t.size, P1, rows, nrows);
+            if (sl >= nrows) continue;
             const cx<W> w = conj(g[(rows[sl] * m2) << tsh]);
             Y[(long long)rows[sl] * P2 + m2] = buf[pad(idx)] * w;
             if (two) Y2[(long long)rows[sl] * P2 + m2] = buf[pad(o2 + idx)] * w;
