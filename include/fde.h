@@ -93,7 +93,10 @@ typedef struct {
     double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2 (right precond.) */
     int max_iters;         /* cap on products with M (inner iterations), >= 1 */
     int precision;         /* fde_precision */
-    double inner_tol;      /* FDE_PREC_F32_IR: relative tolerance of each inner solve */
+    double inner_tol;      /* FDE_PREC_F32_IR: relative tolerance of each inner solve; an
+                              inner solve also stops after 2m products (GMRES(m)) or 50
+                              (PCG), and the refinement loop then judges the correction
+                              by how much it shrank the FP64 residual */
     int max_outer;         /* FDE_PREC_F32_IR: cap on refinement steps */
     int side;              /* fde_side (GMRES only; PCG ignores it) */
     int balance;           /* fde_krylov_solve with count > 1: 0 splits the GPU evenly over the

@@ -11,6 +11,9 @@ namespace fde {
 enum Op : int { kOpSolve = 0, kOpMatvec = 1, kOpTau = 2, kOpMatvecSub = 3 };   // kOpMatvecSub: out -= M in
 enum Mode : int { kModeF64 = 0, kModeF32 = 1, kModeIR = 2 };
 
+// Products with M one inner FP32 PCG solve of the refinement mode may take.
+constexpr int kInnerPcgIters = 50;
+
 struct EngineArgs {
     int op;
     int count;
@@ -114,7 +117,12 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
                 if (!team_sync(t)) return false;
                 SolveState in{};
                 in.iterations = st.iterations;
-                SolveParams sp{a.inner_tol, a.max_iters, a.side, 1};
+                // An FP32 solve that has not reached inner_tol within two restart
+                // cycles is limited by FP32 resolution, not by the Krylov space: more
+                // iterations only chase rounding noise (about 900 for alpha = 1.8 at
+                // n = 65535).  Its correction goes to the contraction test above.
+                const int cap = st.iterations + (I.method == FDE_GMRES ? 2 * I.restart : kInnerPcgIters);
+                SolveParams sp{a.inner_tol, cap < a.max_iters ? cap : a.max_iters, a.side, 1};
                 if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, in, ks, wk)) return false;
                 st.iterations = in.iterations;
                 st.restarts += in.restarts;
