@@ -37,6 +37,9 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 engine launch of this
 # workload (balanced teams), from the ncu capture summarised under profiles/
 F64_LAUNCH_DRAM_BYTES = 239.088896e6 + 548.673536e6
+# FP64 ALU peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_SOURCE = "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz"
 
 
 def parse():
@@ -158,8 +161,7 @@ def run_ours(args, rank, world, device):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    # FP64 ALU peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s)
-    fp64_peak_tflops = 152 * 2 * 2 * 2.07e9 / 1e12
+    fp64_peak_tflops = FP64_PEAK_TFLOPS
 
     results = {}
     from paper_1912_13304_gb300.solver import TimeStepper
@@ -246,7 +248,7 @@ def run_ours(args, rank, world, device):
             # DRAM read + write of one balanced FP64 launch (ncu; profiles/fde_engine_f64_n65535_3alpha.md)
             roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / fp64_peak_tflops, "traffic": F64_LAUNCH_DRAM_BYTES if args.balance else None,
-                    "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz"}
+                    "peak_source": FP64_PEAK_SOURCE}
         else:
             achieved = per_launch_its * bpi / (avg_launch * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -321,6 +323,10 @@ def run_batch(args, device):
                      "outer": sum(i["outer"] for i in infos),
                      "worst_relres": max(i["relres"] for i in infos),
                      "converged": all(i["status"] == fde.OK and i["relres"] <= TOL for i in infos)}
+        if prec == "f64":
+            flops = sum(i["iterations"] * FFTS_PER_ITERATION["pcg"] * fft_flops(2 * (w["n1"] + 1))
+                        for w, i in zip(ws, infos))
+            out[prec]["roofline"] = alu_roofline(flops, t, FP64_PEAK_TFLOPS)
         for p in plans:
             p.close()
     return {"workload": "batch256-1d-const-n255..16383-pcg-shifted-tau", "instances": len(ws),
@@ -330,6 +336,23 @@ def run_batch(args, device):
 # Algorithmic vector passes per iteration of the 2D solves (each pass reads or
 # writes N elements once): PCG with P_hat about 11, GMRES(20) with D_N about 34.
 PASSES_2D = {"pcg": 11, "gmres": 34}
+
+# Real-packed FFTs of one line per iteration: the tau solve's two sine
+# transforms, plus the matvec's forward and one inverse transform (PCG,
+# symmetric multiplier) or two inverse transforms (GMRES, D_+ T x and D_- T^T x).
+FFTS_PER_ITERATION = {"pcg": 4, "gmres": 5}
+
+
+def fft_flops(L: int) -> float:
+    """Flops of one real-packed FFT of L real points (an L/2-point complex FFT
+    plus the pair step), the 2.5 L log2 L of the split-radix count."""
+    return 2.5 * L * math.log2(L)
+
+
+def alu_roofline(flops: float, ms: float, peak_tflops: float) -> dict:
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None, "peak_source": FP64_PEAK_SOURCE}
 
 
 def run_2d(args, device):
@@ -413,6 +436,13 @@ def run_2d(args, device):
                          "schedule": {"ctas": schedule[0], "log_p1": schedule[1]},
                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                       "frac": gbs / hbm_peak, "traffic": None}}
+            if prec == "f64":
+                # the FP64 transforms bound this path, as in 1D: its HBM figure stays beside
+                n1, n2 = w["n1"], w["n2"]
+                flops = inf["iterations"] * FFTS_PER_ITERATION[w["method"]] * (
+                    n2 * fft_flops(2 * (n1 + 1)) + n1 * fft_flops(2 * (n2 + 1)))
+                res[prec]["roofline_hbm"] = res[prec]["roofline"]
+                res[prec]["roofline"] = alu_roofline(flops, t, FP64_PEAK_TFLOPS)
             plan.close()
             del x, b, x0
             torch.cuda.empty_cache()
