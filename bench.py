@@ -36,7 +36,7 @@ TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 engine launch of this
 # workload (balanced teams), from the ncu capture summarised under profiles/
-F64_LAUNCH_DRAM_BYTES = 239.088896e6 + 548.673536e6
+F64_LAUNCH_DRAM_BYTES = 303.106304e6 + 804.658432e6
 # FP64 ALU peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_PEAK_SOURCE = "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz"
