@@ -266,18 +266,66 @@ def run_ours(args, rank, world, device):
     return results
 
 
-def run_batch(args, device):
+def shard_by_cost(costs, world: int) -> list[list[int]]:
+    """Partition instance indices over `world` ranks by cost, longest first
+    onto the least-loaded rank (ties: lower index, lower rank).  Each rank's
+    list is in ascending index order; with one rank it is every index in order."""
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def batch_cost(n: int) -> float:
+    """Relative cost of one constant-coefficient PCG solve of size n: the
+    Case I shifted preconditioner keeps the iteration count flat in n, so the
+    work per solve goes as the line transforms, L log2 L with L = 2(n+1)."""
+    L = 2 * (n + 1)
+    return L * math.log2(L)
+
+
+BATCH_KS = range(8, 15)        # n = 2^k - 1 of the batched workload
+
+
+def batch_job(local: dict, world: int, device) -> dict:
+    """Whole-job figures of the sharded batch (every rank calls it; a
+    collective when world > 1): the slowest rank's launch time, the worst
+    relres and per-size iteration maximum, summed iterations, flops and
+    unknown-iterations, and whether every rank converged.  `max_its_by_k`
+    holds one entry per k of BATCH_KS (0 where a rank has no such size)."""
+    if world == 1:
+        return dict(local)
+    import torch
+    mx = torch.tensor([local["ms_per_launch"], local["worst_relres"]] + list(local["max_its_by_k"]),
+                      dtype=torch.float64, device=device)
+    sm = torch.tensor([local["iterations"], local["outer"], local["unknown_iters"], local["flops"],
+                       0.0 if local["converged"] else 1.0], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return {"ms_per_launch": float(mx[0]), "worst_relres": float(mx[1]),
+            "max_its_by_k": [int(v) for v in mx[2:].tolist()], "iterations": int(sm[0]), "outer": int(sm[1]),
+            "unknown_iters": float(sm[2]), "flops": float(sm[3]), "converged": float(sm[4]) == 0.0}
+
+
+def run_batch(args, device, rank: int = 0, world: int = 1):
     """The batched workload: 256 independent 1D constant-coefficient solves
     (n = 2^k - 1, k ~ U{8..14}; alpha ~ U(1.1, 1.9); d, dt per instance; seed
     2), PCG with each instance's shifted tau preconditioner, relres 1e-8, all
     in one persistent launch (one-CTA teams taking instances from a queue,
     largest first).  Reported per precision path: solves/s and
-    unknown-iterations/s."""
+    unknown-iterations/s.  Under torchrun the instances are sharded over the
+    ranks by cost (no collective on the data path; the 256 solves are the
+    fixed total, strong scaling) and the figures are whole-job ones."""
     import torch
 
     import paper_1912_13304_gb300 as fde
     import workloads
-    ws = workloads.config4()
+    ws_all = workloads.config4()
+    mine = shard_by_cost([batch_cost(w["n1"]) for w in ws_all], world)[rank]
+    ws = [ws_all[i] for i in mine]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     out = {}
     # the workload's own preconditioner (Case I shift) and the default layout:
@@ -311,26 +359,36 @@ def run_batch(args, device):
             torch.cuda.synchronize()
             ms.append(s0.elapsed_time(s1))
         infos = fde.decode_info(info.cpu().numpy().tobytes(), len(ws))
-        t = sum(ms) / len(ms)
-        unk = sum(w["n1"] * i["iterations"] for w, i in zip(ws, infos))
-        by_n = {}
+        max_its = {k: 0 for k in BATCH_KS}
         for w, i in zip(ws, infos):
-            by_n.setdefault(w["n1"], []).append(i["iterations"])
-        out[prec] = {"ms_per_launch": t, "solves_per_s": len(ws) / (t * 1e-3),
-                     "max_iterations_by_n": {str(k): max(v) for k, v in sorted(by_n.items())},
-                     "unknown_iters_per_s": unk / (t * 1e-3),
-                     "iterations": sum(i["iterations"] for i in infos),
-                     "outer": sum(i["outer"] for i in infos),
-                     "worst_relres": max(i["relres"] for i in infos),
-                     "converged": all(i["status"] == fde.OK and i["relres"] <= TOL for i in infos)}
+            k = int(round(math.log2(w["n1"] + 1)))
+            max_its[k] = max(max_its[k], i["iterations"])
+        job = batch_job({"ms_per_launch": sum(ms) / len(ms),
+                         "worst_relres": max((i["relres"] for i in infos), default=0.0),
+                         "max_its_by_k": [max_its[k] for k in BATCH_KS],
+                         "iterations": sum(i["iterations"] for i in infos),
+                         "outer": sum(i["outer"] for i in infos),
+                         "unknown_iters": float(sum(w["n1"] * i["iterations"] for w, i in zip(ws, infos))),
+                         "flops": sum(i["iterations"] * FFTS_PER_ITERATION["pcg"] * fft_flops(2 * (w["n1"] + 1))
+                                      for w, i in zip(ws, infos)),
+                         "converged": all(i["status"] == fde.OK and i["relres"] <= TOL for i in infos)},
+                        world, device)
+        t = job["ms_per_launch"]
+        out[prec] = {"ms_per_launch": t, "solves_per_s": len(ws_all) / (t * 1e-3),
+                     "max_iterations_by_n": {str(2 ** k - 1): v for k, v in zip(BATCH_KS, job["max_its_by_k"])
+                                             if v > 0},
+                     "unknown_iters_per_s": job["unknown_iters"] / (t * 1e-3),
+                     "iterations": job["iterations"],
+                     "outer": job["outer"],
+                     "worst_relres": job["worst_relres"],
+                     "converged": job["converged"]}
         if prec == "f64":
-            flops = sum(i["iterations"] * FFTS_PER_ITERATION["pcg"] * fft_flops(2 * (w["n1"] + 1))
-                        for w, i in zip(ws, infos))
-            out[prec]["roofline"] = alu_roofline(flops, t, FP64_PEAK_TFLOPS)
+            out[prec]["roofline"] = alu_roofline(job["flops"], t, FP64_PEAK_TFLOPS * world)
         for p in plans:
             p.close()
-    return {"workload": "batch256-1d-const-n255..16383-pcg-shifted-tau", "instances": len(ws),
-            "unknowns": sum(w["n1"] for w in ws), "paths": out}
+    return {"workload": "batch256-1d-const-n255..16383-pcg-shifted-tau", "instances": len(ws_all),
+            "unknowns": sum(w["n1"] for w in ws_all), "paths": out,
+            "sharding": "one launch" if world == 1 else f"cost-balanced over {world} ranks (strong scaling)"}
 
 
 # Algorithmic vector passes per iteration of the 2D solves (each pass reads or
@@ -530,12 +588,12 @@ def main():
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     if args.only:
-        out = run_2d(args, device) if args.only == "2d" else run_batch(args, device)
+        out = run_2d(args, device) if args.only == "2d" else run_batch(args, device, rank, world)
         if rank == 0:
             print(json.dumps({"section": args.only, "results": out}), flush=True)
         return
     res = run_ours(args, rank, world, device)
-    batch = run_batch(args, device) if args.batch else None
+    batch = run_batch(args, device, rank, world) if args.batch else None
     two_d = run_2d(args, device) if args.two_d else None
     # headline: the fastest precision path with the workload's preconditioner (the
     # paper's P_F) that met relres 1e-8 on every solve; "+variant" paths use other

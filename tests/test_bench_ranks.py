@@ -55,3 +55,60 @@ def test_single_rank_is_local():
     import torch
     ms, value = bench.job_throughput(80.0, 60, 1, torch.device("cpu"))
     assert ms == 80.0 and value == pytest.approx(60 / 0.080)
+
+
+def _batch_rank(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import bench
+    local = [dict(ms_per_launch=5.0, worst_relres=3e-9, max_its_by_k=[5, 5, 0, 5, 0, 0, 6], iterations=640,
+                  outer=0, unknown_iters=1e6, flops=2e9, converged=True),
+             dict(ms_per_launch=6.0, worst_relres=9e-9, max_its_by_k=[5, 0, 5, 5, 6, 5, 0], iterations=650,
+                  outer=0, unknown_iters=2e6, flops=3e9, converged=False)][rank]
+    job = bench.batch_job(local, world, torch.device("cpu"))
+    dist.barrier()
+    out.put((rank, job))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_combine_the_sharded_batch():
+    """The batch section under torchrun: each rank solves its shard; the job
+    takes the slowest rank's time, sums the work and converges only if every
+    rank did."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in procs), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for _, job in res:
+        assert job["ms_per_launch"] == pytest.approx(6.0)
+        assert job["worst_relres"] == pytest.approx(9e-9)
+        assert job["max_its_by_k"] == [5, 5, 5, 5, 6, 5, 6]
+        assert job["iterations"] == 1290 and job["outer"] == 0
+        assert job["unknown_iters"] == pytest.approx(3e6) and job["flops"] == pytest.approx(5e9)
+        assert job["converged"] is False
+
+
+def test_batch_shards_cover_every_instance_once_and_balance_the_cost():
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads
+    costs = [bench.batch_cost(w["n1"]) for w in workloads.config4()]
+    assert bench.shard_by_cost(costs, 1) == [list(range(len(costs)))]
+    for world in (2, 3, 4, 8):
+        parts = bench.shard_by_cost(costs, world)
+        assert sorted(i for p in parts for i in p) == list(range(len(costs)))
+        assert all(p == sorted(p) for p in parts)
+        loads = [sum(costs[i] for i in p) for p in parts]
+        # longest-first greedy: no rank exceeds the mean by more than one instance's cost
+        assert max(loads) <= sum(costs) / world + max(costs)
+        assert max(loads) / (sum(costs) / world) < 1.01
