@@ -149,7 +149,7 @@ def run_ours(args, rank, world, device):
     fbuild.build()
     fde.lib()
     n = args.n
-    ws = workloads.config2(n=n, alphas=ALPHAS, steps=TIME_STEPS)
+    ws = workloads.var_1d_time_stepping(n=n, alphas=ALPHAS, steps=TIME_STEPS)
     u0_host = [torch.tensor(w["u0"], dtype=torch.float64).pin_memory() for w in ws]
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
@@ -323,7 +323,7 @@ def run_batch(args, device, rank: int = 0, world: int = 1):
 
     import paper_1912_13304_gb300 as fde
     import workloads
-    ws_all = workloads.config4()
+    ws_all = workloads.const_1d_batch()
     mine = shard_by_cost([batch_cost(w["n1"]) for w in ws_all], world)[rank]
     ws = [ws_all[i] for i in mine]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
@@ -434,9 +434,9 @@ def run_2d(args, device):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     out = {}
-    w5 = workloads.config5(steps=1)
+    w5 = workloads.var_2d_time_stepping(steps=1)
     w5cn = dict(w5, time_scheme="cn")
-    for name, w in (("2d-const-n2047-pcg-phat", workloads.config3()),
+    for name, w in (("2d-const-n2047-pcg-phat", workloads.const_2d()),
                     ("2d-var-n4095-gmres20-one-step", w5),
                     ("2d-var-n4095-gmres20-crank-nicolson-step", w5cn)):
         res = {}
@@ -518,7 +518,7 @@ def cpu_baseline_sample(n: int):
 
     import oracle
     import workloads
-    w = workloads.config2(n=n, alphas=(1.8,))[0]
+    w = workloads.var_1d_time_stepping(n=n, alphas=(1.8,))[0]
     h = 1.0 / (n + 1)
     prob = oracle.Problem1D(alpha=w["alpha"], n=n, c0=h ** w["alpha"] / w["dt"], dp=w["dp"], dm=w["dm"])
     P = oracle.Tau1D.for_problem(prob)
@@ -527,7 +527,7 @@ def cpu_baseline_sample(n: int):
     t0 = time.perf_counter()
     res = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, x0=w["u0"], restart=RESTART, tol=TOL, maxiter=cap)
     t = time.perf_counter() - t0
-    ws = workloads.config2(n=4095, alphas=(1.8,))[0]
+    ws = workloads.var_1d_time_stepping(n=4095, alphas=(1.8,))[0]
     hs = 1.0 / 4096
     ps = oracle.Problem1D(alpha=1.8, n=4095, c0=hs ** 1.8 / ws["dt"], dp=ws["dp"], dm=ws["dm"])
     rs = oracle.gmres(ps.matvec, ps.c0 * ws["u0"], Pinv=oracle.Tau1D.for_problem(ps).apply_inverse,

@@ -95,7 +95,7 @@ typedef struct {
     int precision;         /* fde_precision */
     double inner_tol;      /* FDE_PREC_F32_IR: relative tolerance of each inner solve; an
                               inner solve also stops after 2m products (GMRES(m)) or 50
-                              (PCG), and the refinement loop then judges the correction
+                              (PCG), and the refinement loop then measures the correction
                               by how much it shrank the FP64 residual */
     int max_outer;         /* FDE_PREC_F32_IR: cap on refinement steps */
     int side;              /* fde_side (GMRES only; PCG ignores it) */

@@ -102,7 +102,7 @@ def test_batch_shards_cover_every_instance_once_and_balance_the_cost():
     sys.path.insert(0, ROOT)
     import bench
     import workloads
-    costs = [bench.batch_cost(w["n1"]) for w in workloads.config4()]
+    costs = [bench.batch_cost(w["n1"]) for w in workloads.const_1d_batch()]
     assert bench.shard_by_cost(costs, 1) == [list(range(len(costs)))]
     for world in (2, 3, 4, 8):
         parts = bench.shard_by_cost(costs, world)

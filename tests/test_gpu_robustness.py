@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_barrier_wait_runs_out_and_reports_timeout(gpu):
-    w = workloads.config2(n=1023, alphas=(1.5,))[0]
+    w = workloads.var_1d_time_stepping(n=1023, alphas=(1.5,))[0]
     plan = fde.Plan.from_workload(w)
     status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
     st = fde.lib().fde_selftest_barrier_timeout(plan.handle, status.data_ptr(), fde._stream(None))
@@ -31,7 +31,7 @@ def test_barrier_wait_runs_out_and_reports_timeout(gpu):
 @pytest.mark.parametrize("method", ["gmres", "pcg"])
 def test_nan_right_hand_side_reports_nonfinite(gpu, method):
     n = 1023
-    w = workloads.config1(n=n) if method == "pcg" else workloads.config2(n=n, alphas=(1.5,))[0]
+    w = workloads.const_1d(n=n) if method == "pcg" else workloads.var_1d_time_stepping(n=n, alphas=(1.5,))[0]
     plan = fde.Plan.from_workload(w)
     b = np.random.default_rng(3).uniform(-1, 1, n)
     b[n // 3] = np.nan
@@ -42,9 +42,9 @@ def test_nan_right_hand_side_reports_nonfinite(gpu, method):
 @pytest.mark.parametrize("case", ["1d-split", "1d-cta", "2d", "ir"])
 def test_nan_poisoned_workspace_gives_identical_solves(gpu, case):
     if case == "2d":
-        w = workloads.config5(n=255, steps=1)
+        w = workloads.var_2d_time_stepping(n=255, steps=1)
     else:
-        w = workloads.config2(n=16383 if case != "1d-cta" else 1023, alphas=(1.8,))[0]
+        w = workloads.var_1d_time_stepping(n=16383 if case != "1d-cta" else 1023, alphas=(1.8,))[0]
     prec = "f32_ir" if case == "ir" else "f64"
     xs = []
     for fill in (None, 0xFF):
@@ -58,7 +58,7 @@ def test_nan_poisoned_workspace_gives_identical_solves(gpu, case):
 
 
 def test_repeated_solves_are_bit_identical(gpu):
-    ws = workloads.config2(n=16383, alphas=(1.2, 1.8))
+    ws = workloads.var_1d_time_stepping(n=16383, alphas=(1.2, 1.8))
     plans = [fde.Plan.from_workload(w) for w in ws]
     bs = [p.rhs(to_dev(gpu, w["u0"], "f64")) for p, w in zip(plans, ws)]
     runs = []

@@ -29,7 +29,7 @@ def oracle_problem_1d(w):
 @pytest.mark.parametrize("precision", ["f64", "f32_ir"])
 @pytest.mark.parametrize("n", [1, 7, 63, 1023, 4095])
 def test_pcg_case1_matches_oracle(gpu, n, precision):
-    w = workloads.config1(n=n)
+    w = workloads.const_1d(n=n)
     prob = oracle_problem_1d(w)
     b = prob.c0 * w["b"]                  # the workload writes (I + dt h^-a (...)) u = b
     P = oracle.Tau1D.for_problem(prob, shift=True)
@@ -50,7 +50,7 @@ def test_pcg_case1_matches_oracle(gpu, n, precision):
 @pytest.mark.parametrize("alpha", [1.2, 1.8])
 @pytest.mark.parametrize("n", [63, 1023, 4095, 16383])
 def test_gmres_right_variable_coefficients(gpu, n, alpha):
-    w = workloads.config2(n=n, alphas=(alpha,))[0]
+    w = workloads.var_1d_time_stepping(n=n, alphas=(alpha,))[0]
     prob = oracle_problem_1d(w)
     b = prob.c0 * w["u0"]
     P = oracle.Tau1D.for_problem(prob)
@@ -71,7 +71,7 @@ def test_gmres_right_variable_coefficients(gpu, n, alpha):
 def test_gmres_shifted_variable_coefficients(gpu, n, alpha):
     # the shifted variant on the variable-coefficient workload: iterations
     # within +-1 of the oracle's and far fewer than the unshifted P_F's
-    w = workloads.config2(n=n, alphas=(alpha,))[0]
+    w = workloads.var_1d_time_stepping(n=n, alphas=(alpha,))[0]
     prob = oracle_problem_1d(w)
     b = prob.c0 * w["u0"]
     ref = oracle.gmres(prob.matvec, b, Pinv=oracle.Tau1D.for_problem(prob, shift=True).apply_inverse, x0=w["u0"],
@@ -110,7 +110,7 @@ def test_gmres_refinement_fp32_inner(gpu, alpha):
     """FP32 inner GMRES, FP64 outer residual and update: every solve reaches
     the FP64 tolerance and the refined solution matches the tight oracle."""
     n = 4095
-    w = workloads.config2(n=n, alphas=(alpha,))[0]
+    w = workloads.var_1d_time_stepping(n=n, alphas=(alpha,))[0]
     prob = oracle_problem_1d(w)
     b = prob.c0 * w["u0"]
     P = oracle.Tau1D.for_problem(prob)
@@ -132,11 +132,11 @@ def test_pure_fp32_inner_solve(gpu, case):
     from the true one by ~kappa u32) and the solution matches the tight FP64
     oracle to 1e-5."""
     if case == "1d":
-        w = workloads.config1(n=1023)
+        w = workloads.const_1d(n=1023)
         prob = oracle_problem_1d(w)
         P = oracle.Tau1D.for_problem(prob, shift=True)
     else:
-        w = workloads.config3(n=127)
+        w = workloads.const_2d(n=127)
         h = 1.0 / 128
         prob = oracle.Problem2D(alpha=w["alpha"], beta=w["beta"], n1=127, n2=127, c0=h ** w["alpha"] / w["dt"],
                                 sr=h ** w["alpha"] / h ** w["beta"], dp=w["dp"], dm=w["dm"], ep=w["ep"],
@@ -172,7 +172,7 @@ def test_gmres_left_paper_mode_example1(gpu, n):
 
 
 def test_batched_case1_instances(gpu):
-    ws = workloads.config4(count=24, kmin=8, kmax=11)
+    ws = workloads.const_1d_batch(count=24, kmin=8, kmax=11)
     plans, bs, xs, refs = [], [], [], []
     for w in ws:
         prob = oracle_problem_1d(w)
@@ -193,7 +193,7 @@ def test_batched_case1_instances(gpu):
 @pytest.mark.parametrize("precision", ["f64", "f32_ir"])
 @pytest.mark.parametrize("n", [63, 255])
 def test_2d_pcg_shifted(gpu, n, precision):
-    w = workloads.config3(n=n)
+    w = workloads.const_2d(n=n)
     h = 1.0 / (n + 1)
     prob = oracle.Problem2D(alpha=w["alpha"], beta=w["beta"], n1=n, n2=n, c0=h ** w["alpha"] / w["dt"],
                             sr=h ** w["alpha"] / h ** w["beta"], dp=w["dp"], dm=w["dm"], ep=w["ep"], em=w["em"],
@@ -213,7 +213,7 @@ def test_2d_pcg_shifted(gpu, n, precision):
 
 @pytest.mark.parametrize("n", [31, 127])
 def test_2d_gmres_variable(gpu, n):
-    w = workloads.config5(n=n)
+    w = workloads.var_2d_time_stepping(n=n)
     h = 1.0 / (n + 1)
     prob = oracle.Problem2D(alpha=w["alpha"], beta=w["beta"], n1=n, n2=n, c0=h ** w["alpha"] / w["dt"],
                             sr=h ** w["alpha"] / h ** w["beta"], dp=w["dp"], dm=w["dm"], ep=w["ep"], em=w["em"],
@@ -246,7 +246,7 @@ def test_full_size_variable_coefficient_step(gpu):
     split-line path: device relres re-checked by the oracle's direct sums.
     At kappa(M) ~ 1e7 both residual evaluations carry rounding of order
     u ||M|| ||x|| / ||b|| ~ 1e-9, so they agree to that level, not to 1e-3."""
-    w = workloads.config2(alphas=(1.8,))[0]
+    w = workloads.var_1d_time_stepping(alphas=(1.8,))[0]
     prob = oracle_problem_1d(w)
     b = prob.c0 * w["u0"]
     plan = fde.Plan.from_workload(w)
@@ -262,7 +262,7 @@ def test_batched_balanced_teams_match_even_split(gpu):
     # Team sizes from the previous solve's iteration counts change only the
     # reduction order: the same iterations (+-1) and the same solutions.
     import torch
-    ws = workloads.config2(n=16383, alphas=(1.2, 1.5, 1.8))
+    ws = workloads.var_1d_time_stepping(n=16383, alphas=(1.2, 1.5, 1.8))
     plans = [fde.Plan.from_workload(w) for w in ws]
     bs = [plans[i].rhs(to_dev(gpu, w["u0"], "f64")) for i, w in enumerate(ws)]
     xs0 = [to_dev(gpu, w["u0"], "f64") for w in ws]
@@ -294,7 +294,7 @@ def test_graph_time_stepping_replays_the_eager_steps(gpu):
     # reductions), and every replayed step reports convergence.
     import torch
     from paper_1912_13304_gb300.solver import TimeStepper
-    ws = workloads.config2(n=16383, alphas=(1.2, 1.8), steps=3)
+    ws = workloads.var_1d_time_stepping(n=16383, alphas=(1.2, 1.8), steps=3)
     plans = [fde.Plan.from_workload(w) for w in ws]
     u0 = [to_dev(gpu, w["u0"], "f64") for w in ws]
     ue = [x.clone() for x in u0]
@@ -322,7 +322,7 @@ def test_batched_256_instances_full_size(gpu, precision):
     # The full batched workload (n up to 16383, so one-CTA teams also run the
     # split-line layout): every instance converges, and a sample spanning the
     # sizes matches the oracle's PCG iteration counts and residuals.
-    ws = workloads.config4()
+    ws = workloads.const_1d_batch()
     plans = [fde.Plan.from_workload(w, precision=precision) for w in ws]
     bs = [to_dev(gpu, p.c0 * w["b"], "f64") for p, w in zip(plans, ws)]
     xs = [gpu.zeros_like(b) for b in bs]
@@ -344,7 +344,7 @@ def test_batched_256_instances_full_size(gpu, precision):
 
 def test_autotuned_schedule_solves_match_oracle(gpu):
     n = 16383
-    w = workloads.config2(n=n, alphas=(1.5,))[0]
+    w = workloads.var_1d_time_stepping(n=n, alphas=(1.5,))[0]
     prob = oracle_problem_1d(w)
     b = prob.c0 * w["u0"]
     ref = oracle.gmres(prob.matvec, b, Pinv=oracle.Tau1D.for_problem(prob).apply_inverse, x0=w["u0"], restart=30,
@@ -363,7 +363,7 @@ def test_autotuned_schedule_solves_match_oracle(gpu):
 
 def test_autotuned_schedule_full_size_and_2d(gpu):
     # n = 65535: the tuned schedule against the default one (same iterations)
-    w = workloads.config2(alphas=(1.8,))[0]
+    w = workloads.var_1d_time_stepping(alphas=(1.8,))[0]
     infos = []
     for tune in (False, True):
         plan = fde.Plan.from_workload(w)
@@ -374,7 +374,7 @@ def test_autotuned_schedule_full_size_and_2d(gpu):
     assert all(i["status"] == fde.OK and i["relres"] <= 1e-8 for i in infos), infos
     assert abs(infos[0]["iterations"] - infos[1]["iterations"]) <= 1
     # 2D: team size only
-    w2 = workloads.config5(n=255, steps=1)
+    w2 = workloads.var_2d_time_stepping(n=255, steps=1)
     plan = fde.Plan.from_workload(w2, precision="f32_ir")
     ctas, lp1 = plan.autotune()
     assert lp1 == 0 and ctas >= 16
@@ -467,7 +467,7 @@ def test_refinement_switches_to_fp64_when_fp32_corrections_stall(gpu, alpha):
     # FP64 iteration count; FP32 refinement alone needed hundreds more).
     # alpha = 1.2: the FP32 corrections contract and refinement continues.
     n = 16383
-    w = workloads.config2(n=n, alphas=(alpha,))[0]
+    w = workloads.var_1d_time_stepping(n=n, alphas=(alpha,))[0]
     prob = oracle_problem_1d(w)
     b = prob.c0 * w["u0"]
     i64 = fde.Plan.from_workload(w).solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8)

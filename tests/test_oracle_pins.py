@@ -195,7 +195,7 @@ def test_tau_is_toeplitz_minus_hankel(alpha, n):
 # Solvers against LAPACK
 # ----------------------------------------------------------------------------
 
-def _config1_like(n, alpha=1.5):
+def _const_1d_like(n, alpha=1.5):
     h = 1.0 / (n + 1)
     nu = h ** alpha / h
     return Problem1D(alpha=alpha, n=n, c0=nu, dp=np.ones(n), dm=np.ones(n), scheme=GL1)
@@ -203,7 +203,7 @@ def _config1_like(n, alpha=1.5):
 
 @pytest.mark.parametrize("n", [1, 2, 3, 7, 63])
 def test_pcg_matches_lapack(n):
-    prob = _config1_like(n)
+    prob = _const_1d_like(n)
     b = np.random.default_rng(n).uniform(-1, 1, n)
     P = Tau1D.for_problem(prob, shift=True)
     res = pcg(prob.matvec, b, Pinv=P.apply_inverse, tol=1e-14, maxiter=200)
@@ -347,7 +347,7 @@ def test_case1_shifted_pcg_iterations_bounded_in_n():
     counts flat as n grows (config-1 shape: alpha=1.5, d=1, dt=h)."""
     its = []
     for n in (63, 255, 1023, 4095):
-        prob = _config1_like(n)
+        prob = _const_1d_like(n)
         b = np.random.default_rng(0).uniform(-1, 1, n)
         P = Tau1D.for_problem(prob, shift=True)
         res = pcg(prob.matvec, b, Pinv=P.apply_inverse, tol=1e-8)
@@ -365,7 +365,7 @@ def test_shifted_variable_coefficient_variant_bounded_and_cheaper():
     import workloads
     its_s, its_u = [], []
     for n in (255, 1023, 4095):
-        w = workloads.config2(n=n, alphas=(1.2,))[0]
+        w = workloads.var_1d_time_stepping(n=n, alphas=(1.2,))[0]
         h = 1.0 / (n + 1)
         prob = Problem1D(alpha=1.2, n=n, c0=h ** 1.2 / w["dt"], dp=w["dp"], dm=w["dm"])
         b = prob.c0 * w["u0"]
@@ -434,7 +434,7 @@ def test_planted_index_shift_breaks_hankel_pin():
 
 def test_planted_missing_shift_breaks_bounded_iterations():
     n = 1023
-    prob = _config1_like(n)
+    prob = _const_1d_like(n)
     b = np.random.default_rng(0).uniform(-1, 1, n)
     P = Tau1D.for_problem(prob, shift=False)      # plant: unshifted symbol
     res = pcg(prob.matvec, b, Pinv=P.apply_inverse, tol=1e-8)

@@ -1,4 +1,6 @@
-"""Seeded synthetic inputs shaped like the five benchmark workloads.
+"""Seeded synthetic inputs shaped like the five benchmark workloads (1D constant
+coefficients, 1D variable-coefficient time stepping, 2D constant coefficients,
+a batch of 1D constant-coefficient solves, 2D variable-coefficient time stepping).
 
 This module is shared by the oracle and the CUDA path and holds none of the
 method's arithmetic: it only lays out grids, evaluates the coefficient and
@@ -22,7 +24,7 @@ def grid(n: int, length: float = 1.0):
     return h, h * np.arange(1, n + 1, dtype=np.float64)
 
 
-def config1(n: int = 1023, alpha: float = 1.5, seed: int = 0) -> dict:
+def const_1d(n: int = 1023, alpha: float = 1.5, seed: int = 0) -> dict:
     """1D constant coefficients d+ = d- = 1 on [0,1], one implicit-Euler step
     with dt = h, rhs uniform[-1,1] (seed 0, n draws), PCG with the shifted
     (Case I) tau preconditioner, relres 1e-8, FP64."""
@@ -35,7 +37,7 @@ def config1(n: int = 1023, alpha: float = 1.5, seed: int = 0) -> dict:
                 order="tau_d", restart=0, tol=1e-8, steps=1)
 
 
-def config2(n: int = 65535, alphas=(1.2, 1.5, 1.8), steps: int = 20, dt: float = 1.0 / 512,
+def var_1d_time_stepping(n: int = 65535, alphas=(1.2, 1.5, 1.8), steps: int = 20, dt: float = 1.0 / 512,
             seed: int = 0) -> list[dict]:
     """1D variable coefficients d+ = 1 + x^2, d- = 1 + (1-x)^2 on [0,1],
     implicit Euler with dt = 1/512, u0 = x^2 (1-x)^2 + uniform[-1e-3, 1e-3]
@@ -54,7 +56,7 @@ def config2(n: int = 65535, alphas=(1.2, 1.5, 1.8), steps: int = 20, dt: float =
     return out
 
 
-def config3(n: int = 2047, alpha: float = 1.5, beta: float = 1.7, seed: int = 1) -> dict:
+def const_2d(n: int = 2047, alpha: float = 1.5, beta: float = 1.7, seed: int = 1) -> dict:
     """2D constant coefficients d+- = e+- = 1 on the unit square, one implicit
     step with dt = h, rhs uniform[-1,1] (seed 1, N draws, x fastest), WSGD
     weights, PCG with P_hat (shifted, no D)."""
@@ -68,7 +70,7 @@ def config3(n: int = 2047, alpha: float = 1.5, beta: float = 1.7, seed: int = 1)
                 order="tau_d", restart=0, tol=1e-8, steps=1)
 
 
-def config4(count: int = 256, kmin: int = 8, kmax: int = 14, seed: int = 2) -> list[dict]:
+def const_1d_batch(count: int = 256, kmin: int = 8, kmax: int = 14, seed: int = 2) -> list[dict]:
     """Independent 1D constant-coefficient solves.  For each instance, in order,
     from one generator (seed 2): k ~ U{kmin..kmax} (n = 2^k - 1),
     alpha ~ U(1.1, 1.9), d ~ U[0.5, 2] (d+ = d- = d), dt = U[0.5, 2] * h, then
@@ -91,7 +93,7 @@ def config4(count: int = 256, kmin: int = 8, kmax: int = 14, seed: int = 2) -> l
     return out
 
 
-def config5(n: int = 4095, alpha: float = 1.3, beta: float = 1.8, steps: int = 50,
+def var_2d_time_stepping(n: int = 4095, alpha: float = 1.3, beta: float = 1.8, steps: int = 50,
             dt: float = 1.0 / 256) -> dict:
     """2D variable coefficients d+ = 1+x+y, d- = 2-x, e+ = 1+xy, e- = 1+y^2 on
     the unit square, u0 = sin(pi x) sin(pi y), f = 0, implicit Euler dt = 1/256,
