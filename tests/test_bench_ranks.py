@@ -112,3 +112,16 @@ def test_batch_shards_cover_every_instance_once_and_balance_the_cost():
         # longest-first greedy: no rank exceeds the mean by more than one instance's cost
         assert max(loads) <= sum(costs) / world + max(costs)
         assert max(loads) / (sum(costs) / world) < 1.01
+
+
+def test_all_cores_oracle_sample_runs_one_process_per_core():
+    """The all-cores CPU baseline: the oracle sample in spawned worker
+    processes at once (one BLAS thread each), every worker counted."""
+    sys.path.insert(0, ROOT)
+    import bench
+    one = bench.oracle_sample(1023, cap=3)
+    assert one[1] == 3 and one[0] > 0
+    r = bench.all_cores_sample(1023, 5, timeout_s=120, cores=2)
+    assert r["cores"] == 2 and r["value"] > 0
+    # two workers at once deliver at most twice a single worker's rate
+    assert r["value"] <= 2.0 * 3 / (one[0] * 5) * 3
