@@ -166,6 +166,38 @@ def test_tau_eigenvectors():
     np.testing.assert_allclose(tau @ S, S @ np.diag(f), atol=1e-13)
 
 
+@pytest.mark.parametrize("n1,n2,a,b", [(7, 15, 2, 5), (15, 7, 14, 1), (2047, 3, 1000, 2), (5, 1500, 3, 777)])
+@pytest.mark.parametrize("kind", ["tau_d", "d_tau_const", "shift"])
+def test_tau2d_inverse_on_separable_sine_vectors(n1, n2, a, b, kind):
+    """Sec. 3.2: (S (x) S) diagonalises tau(F) in 2D, so the vector
+    sin(j theta_2b) sin(i theta_1a), laid out x fastest, is an eigenvector of
+    P^-1 with eigenvalue 1 / (D F(theta_1a, theta_2b)).  The vector is built
+    here from sin() directly; n1 != n2 catches a transposed grid, and the
+    sizes above 1024 take the oracle's library-DST path."""
+    alpha, beta, c0, sr = 1.5, 1.7, 0.3, 4.6
+    x1 = np.arange(1, n1 + 1)[None, :] / (n1 + 1)
+    x2 = np.arange(1, n2 + 1)[:, None] / (n2 + 1)
+    if kind == "tau_d":
+        dp, dm, ep, em = 1 + x1 + x2, 2 - x1 + 0 * x2, 1 + x1 * x2, 1 + x2 ** 2 + 0 * x1
+    else:
+        dp = dm = np.full((n2, n1), 1.3)
+        ep = em = np.full((n2, n1), 0.9)       # D = 1.1 for the D tau order
+    prob = Problem2D(alpha=alpha, beta=beta, n1=n1, n2=n2, c0=c0, sr=sr, dp=dp, dm=dm, ep=ep, em=em)
+    order = ORDER_D_TAU if kind == "d_tau_const" else ORDER_TAU_D
+    P = Tau2D.for_problem(prob, shift=kind == "shift", order=order)
+    t1, t2 = a * np.pi / (n1 + 1), b * np.pi / (n2 + 1)
+    v = (np.sin(np.arange(1, n2 + 1) * t2)[:, None] * np.sin(np.arange(1, n1 + 1) * t1)[None, :]).reshape(-1)
+    qa, qb = float(symbol_q(alpha, t1)), float(symbol_q(beta, t2))
+    if kind == "shift":
+        lam = 1.0 / (c0 + 1.3 * qa + sr * 0.9 * qb)
+    else:
+        D = 0.25 * (dp + dm + ep + em)
+        lam = 1.0 / ((qa + sr * qb) * D.reshape(-1))
+    z = P.apply_inverse(v)
+    ref = lam * v
+    assert np.max(np.abs(z - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("alpha,n", [(1.5, 15), (1.2, 16), (1.8, 31)])
 def test_tau_is_toeplitz_minus_hankel(alpha, n):
     """For symmetric Toeplitz A with first column c, tau(A) = A - H with the
