@@ -34,8 +34,6 @@ FDE_HD int max_lines(int Np, int nbuf, int bytes, int extra_real = 0) {
     return (int)((bytes - 64) / per);
 }
 
-FDE_HD int pow2_floor(int v) { int p = 1; while (p * 2 <= v) p *= 2; return p; }
-
 // ---------------------------------------------------------------------------
 // Multipliers
 // ---------------------------------------------------------------------------
