@@ -125,3 +125,19 @@ def test_all_cores_oracle_sample_runs_one_process_per_core():
     assert r["cores"] == 2 and r["value"] > 0
     # two workers at once deliver at most twice a single worker's rate
     assert r["value"] <= 2.0 * 3 / (one[0] * 5) * 3
+
+
+def test_algorithmic_flop_counts_match_the_hand_counts():
+    """The bench's FFT flop accounting against counts made by hand from the
+    transforms per iteration: n = 65535 GMRES about 28 MFLOP; 2047^2 PCG
+    about 2.0 GFLOP; 4095^2 GMRES about 10.9 GFLOP."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.algorithmic_per_iteration(65535, 8)[1] == pytest.approx(27.85e6, rel=1e-3)
+    pcg2d = bench.FFTS_PER_ITERATION["pcg"] * 2 * 2047 * bench.fft_flops(4096)
+    gmres2d = bench.FFTS_PER_ITERATION["gmres"] * 2 * 4095 * bench.fft_flops(8192)
+    assert pcg2d == pytest.approx(2.013e9, rel=1e-3)
+    assert gmres2d == pytest.approx(10.90e9, rel=1e-3)
+    r = bench.alu_roofline(gmres2d, 1000.0, bench.FP64_PEAK_TFLOPS)
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(gmres2d / 1e12)
+    assert bench.FP64_PEAK_TFLOPS == pytest.approx(1.25856)
