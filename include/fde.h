@@ -202,8 +202,11 @@ fde_status fde_step_rhs(const fde_plan* plan, const double* u_prev, const double
  * problem does not fit the fixed scratch).  FDE_ECUDA if setup or a launch
  * fails.
  * Setup: the first call on each device (made with that device current)
- * resolves the scratch's device address once; make that first call before
- * any stream capture.
+ * resolves the scratch's device address with cudaGetSymbolAddress, once, and
+ * caches it under the id of the current CUDA context; make that first call
+ * before any stream capture.  After cudaDeviceReset (or with another context
+ * current on the device) the context id differs, and the next call resolves
+ * the address again; that call too should come before any capture.
  * No part of the scratch needs to start at zero: every call writes each
  * scratch word it reads before reading it.
  * Calls that overlap in time on one device (on different streams, or from
@@ -245,12 +248,17 @@ fde_status fde_plan_set_schedule(fde_plan* plan, int ctas, int log_p1, void* str
 fde_status fde_autotune(fde_plan* plan, void* stream, int* ctas, int* log_p1);
 
 /*
- * Failure-path self-test (no counterpart in the paper): one CTA enters a
- * two-CTA team barrier on the plan's sync area with a bound of 2e6 clock
- * cycles (about 1 ms); the second member is never launched.  The bounded wait
- * must run out and report it: *status_dev (device int) receives FDE_ETIMEOUT,
- * the same status a solve reports when a team member stops arriving.  The
- * sync area is cleared before and after.  Asynchronous on `stream`.
+ * Failure-path self-test (no counterpart in the paper) of the bounded team
+ * barrier and of the launch-wide wind-down after a timeout.  Two CTAs each
+ * enter a two-CTA team barrier of their own on the plan's sync area; the
+ * partners are never launched.  CTA 0 waits with a bound of 2e6 clock cycles
+ * (about 1 ms): its wait runs out and raises the launch's abort flag.  CTA 1
+ * waits with the solver's full bound (about 2 s) but must see the abort flag
+ * on its next poll and return too.  status_dev: device array of 2 ints that
+ * receive FDE_ETIMEOUT for each CTA, the status a solve reports when a team
+ * member stops arriving; the launch ends within about 1 ms plus one poll, not
+ * after CTA 1's full bound.  The sync area is cleared before and after.
+ * Asynchronous on `stream`.
  */
 fde_status fde_selftest_barrier_timeout(const fde_plan* plan, int* status_dev, void* stream);
 

@@ -44,7 +44,7 @@ __all__ = [
     "symbol_g", "symbol_w", "symbol_p", "symbol_q", "scheme_symbol", "tau_grid",
     "sine_matrix", "tau_matrix", "Problem1D", "Problem2D", "Tau1D", "Tau2D",
     "pcg", "gmres", "KrylovResult", "preconditioned_condition_number",
-    "apply_sine_fast", "ORDER_TAU_D", "ORDER_D_TAU", "ORDER_TAU_DF", "GL1", "WSGD2",
+    "apply_sine_fast", "set_fft_workers", "ORDER_TAU_D", "ORDER_D_TAU", "ORDER_TAU_DF", "GL1", "WSGD2",
 ]
 
 GL1 = "gl1"      # first-order shifted Grunwald weights g_k (Sec. 1.2)
@@ -164,7 +164,34 @@ def apply_sine_fast(v: np.ndarray, axis: int = -1) -> np.ndarray:
     it to ``sine_matrix``.
     """
     import scipy.fft
-    return scipy.fft.dst(v, type=1, norm="ortho", axis=axis)
+    return scipy.fft.dst(v, type=1, norm="ortho", axis=axis, workers=_fft_workers())
+
+
+def _convolve_fft(a: np.ndarray, b: np.ndarray, axis: int = -1) -> np.ndarray:
+    """Full linear convolution (a * b)[k] = sum_j a[k-j] b[j] along `axis`, by
+    the library real FFT of a length >= len(a) + len(b) - 1 (zero padding, so
+    no wrap-around).  `a` broadcasts against `b` on the other axis."""
+    import scipy.fft
+    la, lb = a.shape[axis], b.shape[axis]
+    L = scipy.fft.next_fast_len(la + lb - 1, real=True)
+    A = scipy.fft.rfft(a, n=L, axis=axis, workers=_fft_workers())
+    B = scipy.fft.rfft(b, n=L, axis=axis, workers=_fft_workers())
+    out = scipy.fft.irfft(A * B, n=L, axis=axis, workers=_fft_workers())
+    idx = [slice(None)] * out.ndim
+    idx[axis] = slice(0, la + lb - 1)
+    return out[tuple(idx)]
+
+
+_WORKERS = [1]
+
+
+def _fft_workers() -> int:
+    return _WORKERS[0]
+
+
+def set_fft_workers(k: int) -> None:
+    """Threads the library FFT of the fast ("fft") operators may use (1 by default)."""
+    _WORKERS[0] = max(1, int(k))
 
 
 # ----------------------------------------------------------------------------
@@ -209,7 +236,10 @@ class Problem1D:
 
         method="dense" (default up to n = 4096): the dense T.  method="direct":
         the same Toeplitz sums evaluated by direct (non-FFT) convolution of the
-        weight sequence with x, (T x)_i = -sum_j w_{i-j+1} x_j.
+        weight sequence with x, (T x)_i = -sum_j w_{i-j+1} x_j.  method="fft":
+        the same convolutions computed by the library FFT (the fast oracle used
+        at full workload sizes and as the timed CPU baseline; pinned to the
+        dense and direct forms).
         """
         x = np.asarray(x, dtype=np.float64)
         n = self.n
@@ -217,9 +247,10 @@ class Problem1D:
             T = self.T()
             return self.c0 * x + self.dp * (T @ x) + self.dm * (T.T @ x)
         w = self.weights()
-        full = np.convolve(w, x)                 # full[k] = sum_j w[k-j] x_j
+        conv = _convolve_fft if method == "fft" else np.convolve
+        full = conv(w, x)                        # full[k] = sum_j w[k-j] x_j
         Tx = -full[1:n + 1]                      # k = i + 1
-        fullr = np.convolve(w, x[::-1])          # (T^T x)_i = -sum_j w[j-i+1] x_j
+        fullr = conv(w, x[::-1])                 # (T^T x)_i = -sum_j w[j-i+1] x_j
         Ttx = -fullr[n - np.arange(n)]
         return self.c0 * x + self.dp * Tx + self.dm * Ttx
 
@@ -295,10 +326,27 @@ class Problem2D:
             out[t] = self.c0 * U[j, i] + ax + self.sr * ay
         return out
 
-    def matvec(self, x: np.ndarray) -> np.ndarray:
+    def matvec(self, x: np.ndarray, method: str = "dense") -> np.ndarray:
         """The Kronecker products applied as matrix products on the (n2, n1)
-        grid: (I (x) A) u <-> U A^T, (B (x) I) u <-> B U."""
+        grid: (I (x) A) u <-> U A^T, (B (x) I) u <-> B U.
+
+        method="fft": the same Toeplitz sums along every x line and y line as
+        linear convolutions with the weights, computed by the library FFT (for
+        full-size planes, where the dense products cost n^3 per axis)."""
         U = np.asarray(x, dtype=np.float64).reshape(self.n2, self.n1)
+        if method == "fft":
+            wa = scheme_weights(self.alpha, self.n1 + 1, self.scheme)
+            wb = scheme_weights(self.beta, self.n2 + 1, self.scheme)
+            n1, n2 = self.n1, self.n2
+            # rows: (T_a u_j)_i = -sum_k w_{i-k+1} U[j, k] and the transpose
+            fx = _convolve_fft(wa[None, :], U, axis=1)
+            fxr = _convolve_fft(wa[None, :], U[:, ::-1], axis=1)
+            Tax, Tatx = -fx[:, 1:n1 + 1], -fxr[:, n1 - np.arange(n1)]
+            fy = _convolve_fft(wb[:, None], U, axis=0)
+            fyr = _convolve_fft(wb[:, None], U[::-1, :], axis=0)
+            Tby, Tbty = -fy[1:n2 + 1, :], -fyr[n2 - np.arange(n2), :]
+            Y = (self.c0 * U + self.dp * Tax + self.dm * Tatx + self.sr * (self.ep * Tby + self.em * Tbty))
+            return Y.reshape(-1)
         Ta, Tb = self.Ta(), self.Tb()
         Y = (self.c0 * U + self.dp * (U @ Ta.T) + self.dm * (U @ Ta)
              + self.sr * (self.ep * (Tb @ U) + self.em * (Tb.T @ U)))

@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>   // CUcontext and CUresult (types only)
+
 #include "launch.h"
 
 using namespace fde;
@@ -849,20 +851,67 @@ static __device__ __align__(256) unsigned char g_matvec_scratch[FDE_MATVEC_NOALL
 
 namespace {
 
-std::mutex g_scratch_mu;
-unsigned char* g_scratch_ptr[64];
+// The driver's context calls, reached through the runtime (no link against
+// the driver library).  cuCtxGetId gives an id that is unique for the
+// process's lifetime, so a context created after cudaDeviceReset never
+// matches one whose module instance has gone, even if its handle is reused.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
 
-// Device address of g_matvec_scratch on `dev` (the current device), resolved once.
+struct ScratchSlot {
+    unsigned long long ctx_id;   // 0: not resolved
+    unsigned char* ptr;
+};
+
+std::mutex g_scratch_mu;
+ScratchSlot g_scratch[64];
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Id of the context current on this thread, 0 if none is current yet.
+cudaError_t current_context_id(unsigned long long* id) {
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorUnknown;
+    if (!ctx) return cudaSuccess;
+    return g_ctx_get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+}
+
+// Device address of g_matvec_scratch in the context current on `dev`: resolved
+// with cudaGetSymbolAddress on the first call in that context (once per device
+// in normal use) and cached under the context's id.
 cudaError_t matvec_scratch(int dev, unsigned char** out) {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long id = 0;
+    cudaError_t e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    ScratchSlot& slot = g_scratch[dev];
+    if (id == 0 || slot.ctx_id != id) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_scratch);
+        e = cudaGetSymbolAddress(&p, g_matvec_scratch);   // makes the primary context current if none was
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+        if (id == 0) {
+            e = current_context_id(&id);
+            if (e != cudaSuccess) return e;
+        }
+        slot.ctx_id = id;
+        slot.ptr = static_cast<unsigned char*>(p);
     }
-    *out = g_scratch_ptr[dev];
+    *out = slot.ptr;
     return cudaSuccess;
 }
 
@@ -1177,20 +1226,24 @@ extern "C" fde_status fde_autotune(fde_plan* p, void* stream, int* ctas_out, int
 
 namespace {
 
-// One CTA joins a team of two on the plan's sync area with a short wait
-// bound; the second member is never launched, so the wait runs out and the
-// barrier must report it (abort flag set, false returned) instead of hanging.
-__global__ void k_barrier_selftest(SyncArea* sync, long long bound, int* status) {
+// Two CTAs, each the only member that arrives at its own team barrier (team i
+// of two CTAs on the plan's sync area; the partners are never launched).  CTA
+// 0 waits with a short bound, which runs out and raises the launch's abort
+// flag.  CTA 1 waits with the full bound (about 2 s), but must notice the
+// abort flag on its next poll and return as well.  status[i] receives CTA i's
+// result.
+__global__ void k_barrier_selftest(SyncArea* sync, long long short_bound, int* status) {
+    const int i = blockIdx.x;
     Team t;
     t.rank = 0;
     t.size = 2;
-    t.count = &sync->bar_count[0];
-    t.gen = &sync->bar_gen[0];
+    t.count = &sync->bar_count[i];
+    t.gen = &sync->bar_gen[i];
     t.partial = sync->partial;
     t.abort_flag = &sync->abort_flag;
     t.sync = sync;
-    const bool ok = team_sync(t, bound);
-    if (threadIdx.x == 0) *status = ok ? FDE_OK : FDE_ETIMEOUT;
+    const bool ok = team_sync(t, i == 0 ? short_bound : kBarrierCycles);
+    if (threadIdx.x == 0) status[i] = ok ? FDE_OK : FDE_ETIMEOUT;
 }
 
 }  // namespace
@@ -1199,7 +1252,7 @@ extern "C" fde_status fde_selftest_barrier_timeout(const fde_plan* p, int* statu
     if (!p || !status_dev) return FDE_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(p->sync_dev, 0, offsetof(SyncArea, partial), st) != cudaSuccess) return FDE_ECUDA;
-    k_barrier_selftest<<<1, kThreads, 0, st>>>(p->sync_dev, 2000000LL, status_dev);
+    k_barrier_selftest<<<2, kThreads, 0, st>>>(p->sync_dev, 2000000LL, status_dev);
     if (cudaGetLastError() != cudaSuccess) return FDE_ECUDA;
     // leave the sync area clean for the plan's next launch
     if (cudaMemsetAsync(p->sync_dev, 0, offsetof(SyncArea, partial), st) != cudaSuccess) return FDE_ECUDA;

@@ -8,7 +8,8 @@
 namespace fde {
 
 // ~2 s at GB300 clocks.  A barrier that waits longer records FDE_ETIMEOUT in
-// the launch's abort flag and every CTA of the launch winds down.
+// the launch's abort flag; CTAs waiting at any barrier see the flag on their
+// next poll and every CTA of the launch winds down.
 constexpr long long kBarrierCycles = 4000000000LL;
 
 struct Team {
@@ -76,8 +77,16 @@ FDE_D bool team_sync(const Team& t, long long bound = kBarrierCycles) {
             atomicExch(t.count, 0u);
             atom_add_release_gpu(t.gen, 1u);
         } else {
+            // wait for the release of this generation; give up when the bound
+            // runs out (and raise the launch's abort flag) or when another
+            // team's barrier already has, so every CTA winds down within one
+            // poll of the first timeout
             const long long t0 = clock64();
             while (ld_acquire_gpu(t.gen) == g) {
+                if (ld_acquire_gpu(t.abort_flag) != 0u) {
+                    ok = 0;
+                    break;
+                }
                 if (clock64() - t0 > bound) {
                     ok = 0;
                     atomicExch(t.abort_flag, 1u);

@@ -17,7 +17,23 @@ import paper_1912_13304_gb300 as fde
 
 pytestmark = pytest.mark.gpu
 
-TOL = {("mv", "f64"): 1e-11, ("tau", "f64"): 1e-10, ("mv", "f32"): 2e-5, ("tau", "f32"): 5e-4}
+# Unit roundoff of each precision and the constant C of the bound
+# C u log2(L): an L-point FFT's rounding error grows like u log2 L relative to
+# the largest entry.  For the tau solve the division by the symbol samples
+# amplifies the transform errors and the signal alike (both sit in the
+# smoothest sine modes), so the relative error keeps the same form.
+UNIT = {"f64": 2.0 ** -53, "f32": 2.0 ** -24}
+TOL_C = {("mv", "f64"): 5300.0, ("tau", "f64"): 53000.0, ("mv", "f32"): 20.0, ("tau", "f32"): 490.0}
+
+
+def tol(op, dtype, L):
+    """Bound on the relative max-norm error of one operator application whose
+    transforms have L real points per line."""
+    return TOL_C[(op, dtype)] * UNIT[dtype] * max(np.log2(L), 1.0)
+
+
+def L1(n):
+    return 2 * (n + 1)
 
 
 def rel_err(a, b):
@@ -63,7 +79,7 @@ def test_matvec_1d(gpu, n, kind, dtype):
     x = np.random.default_rng(n).uniform(-1, 1, n)
     y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
     ref = prob.matvec(x, "direct" if n > 4096 else "dense")
-    assert rel_err(y, ref) < TOL[("mv", dtype)]
+    assert rel_err(y, ref) < tol("mv", dtype, L1(n))
 
 
 @pytest.mark.parametrize("weights", ["gl1", "wsgd2"])
@@ -85,7 +101,7 @@ def test_tau_1d(gpu, n, variant, dtype):
     P = oracle.Tau1D.for_problem(prob, shift=variant == "shift", order="d_tau" if variant == "d_tau" else "tau_d")
     r = np.random.default_rng(n + 1).uniform(-1, 1, n)
     z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
-    assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
+    assert rel_err(z, P.apply_inverse(r)) < tol("tau", dtype, L1(n))
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -96,7 +112,7 @@ def test_tau_1d_ftilde(gpu, n, dtype):
     P = oracle.Tau1D.for_problem(prob, order="tau_df")
     r = np.random.default_rng(n + 9).uniform(-1, 1, n)
     z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
-    assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
+    assert rel_err(z, P.apply_inverse(r)) < tol("tau", dtype, L1(n))
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -109,7 +125,7 @@ def test_tau_1d_shifted_variable_coefficients(gpu, n, order, dtype):
     P = oracle.Tau1D.for_problem(prob, shift=True, order=order)
     r = np.random.default_rng(n + 5).uniform(-1, 1, n)
     z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
-    assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
+    assert rel_err(z, P.apply_inverse(r)) < tol("tau", dtype, L1(n))
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -124,10 +140,10 @@ def test_full_size_1d_line_split_across_ctas(gpu, dtype):
     rows = np.concatenate([[0, 1, 2, n // 2, n - 2, n - 1], rng.integers(0, n, 40)])
     ref = prob.matvec_rows(x, rows)
     scale = np.max(np.abs(prob.matvec_rows(x, rng.integers(0, n, 200))))
-    assert np.max(np.abs(y[rows] - ref)) / scale < TOL[("mv", dtype)]
+    assert np.max(np.abs(y[rows] - ref)) / scale < tol("mv", dtype, L1(n))
     P = oracle.Tau1D.for_problem(prob)
     z = plan.tau(to_dev(gpu, x, dtype)).double().cpu().numpy()
-    assert rel_err(z, P.apply_inverse(x)) < TOL[("tau", dtype)]
+    assert rel_err(z, P.apply_inverse(x)) < tol("tau", dtype, L1(n))
 
 
 SIZES_2D = [(1, 1), (3, 7), (15, 31), (63, 63), (127, 255), (511, 127)]
@@ -159,7 +175,7 @@ def test_matvec_2d(gpu, n1, n2, kind, dtype):
     plan, prob = make_2d(gpu, n1, n2, kind)
     x = np.random.default_rng(n1 * n2).uniform(-1, 1, n1 * n2)
     y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
-    assert rel_err(y, prob.matvec(x)) < TOL[("mv", dtype)]
+    assert rel_err(y, prob.matvec(x)) < tol("mv", dtype, 2 * (max(n1, n2) + 1))
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -172,14 +188,17 @@ def test_tau_2d(gpu, n1, n2, variant, dtype):
     P = oracle.Tau2D.for_problem(prob, shift=variant == "shift", order=order)
     r = np.random.default_rng(n1 + n2).uniform(-1, 1, n1 * n2)
     z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
-    assert rel_err(z, P.apply_inverse(r)) < TOL[("tau", dtype)]
+    assert rel_err(z, P.apply_inverse(r)) < tol("tau", dtype, 2 * (max(n1, n2) + 1))
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_full_size_2d_plane(gpu, dtype):
-    """4095 x 4095 variable coefficients: sampled entries of M x by their
-    definition; the tau solve in full through the library DST-I."""
-    n = 4095
+@pytest.mark.parametrize("n", [2047, 4095])
+def test_full_size_2d_plane(gpu, n, dtype):
+    """2047^2 and 4095^2 variable coefficients (L = 4096 and 8192 per axis):
+    sampled entries of M x by their row definition, the whole product against
+    the oracle's FFT-convolution form, and the whole tau solve through the
+    library DST-I."""
+    import os
     plan, prob = make_2d(gpu, n, n, "var")
     rng = np.random.default_rng(5)
     x = rng.uniform(-1, 1, n * n)
@@ -188,10 +207,15 @@ def test_full_size_2d_plane(gpu, dtype):
     cols = np.concatenate([[0, n - 1, 0, n - 1, n // 3], rng.integers(0, n, 30)])
     ref = prob.matvec_entries(x, rows, cols)
     scale = np.max(np.abs(ref))
-    assert np.max(np.abs(y.reshape(n, n)[rows, cols] - ref)) / scale < TOL[("mv", dtype)]
-    P = oracle.Tau2D.for_problem(prob)
-    z = plan.tau(to_dev(gpu, x, dtype)).double().cpu().numpy()
-    assert rel_err(z, P.apply_inverse(x)) < TOL[("tau", dtype)]
+    assert np.max(np.abs(y.reshape(n, n)[rows, cols] - ref)) / scale < tol("mv", dtype, 2 * (n + 1))
+    oracle.set_fft_workers(os.cpu_count() or 1)
+    try:
+        assert rel_err(y, prob.matvec(x, "fft")) < tol("mv", dtype, 2 * (n + 1))
+        P = oracle.Tau2D.for_problem(prob)
+        z = plan.tau(to_dev(gpu, x, dtype)).double().cpu().numpy()
+        assert rel_err(z, P.apply_inverse(x)) < tol("tau", dtype, 2 * (n + 1))
+    finally:
+        oracle.set_fft_workers(1)
 
 
 def test_step_rhs(gpu):
@@ -229,13 +253,13 @@ def test_every_split_schedule_1d(gpu, n, dtype):
                 continue
             tried += 1
             y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
-            assert np.max(np.abs(y[rows] - ref_rows)) / scale < TOL[("mv", dtype)], (lp1, ctas)
+            assert np.max(np.abs(y[rows] - ref_rows)) / scale < tol("mv", dtype, L1(n)), (lp1, ctas)
             z = plan.tau(to_dev(gpu, x, dtype)).double().cpu().numpy()
-            assert rel_err(z, z_ref) < TOL[("tau", dtype)], (lp1, ctas)
+            assert rel_err(z, z_ref) < tol("tau", dtype, L1(n)), (lp1, ctas)
     assert tried >= 2
     plan.set_schedule(0, 0)
     y = plan.matvec(to_dev(gpu, x, dtype)).double().cpu().numpy()
-    assert np.max(np.abs(y[rows] - ref_rows)) / scale < TOL[("mv", dtype)]
+    assert np.max(np.abs(y[rows] - ref_rows)) / scale < tol("mv", dtype, L1(n))
 
 
 def test_schedule_validation(gpu):

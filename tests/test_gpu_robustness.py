@@ -15,13 +15,20 @@ pytestmark = pytest.mark.gpu
 
 
 def test_barrier_wait_runs_out_and_reports_timeout(gpu):
+    # CTA 0's short wait runs out; CTA 1, waiting on another team's barrier
+    # with the full ~2 s bound, must notice the abort flag and return at once
     w = workloads.var_1d_time_stepping(n=1023, alphas=(1.5,))[0]
     plan = fde.Plan.from_workload(w)
-    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    status = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
     st = fde.lib().fde_selftest_barrier_timeout(plan.handle, status.data_ptr(), fde._stream(None))
+    e1.record()
     assert st == fde.OK
     torch.cuda.synchronize()
-    assert int(status.item()) == fde.ETIMEOUT
+    assert status.tolist() == [fde.ETIMEOUT, fde.ETIMEOUT]
+    assert e0.elapsed_time(e1) < 200.0, e0.elapsed_time(e1)
     # the plan is usable afterwards
     b = plan.rhs(to_dev(gpu, w["u0"], "f64"))
     info = plan.solve(b, x=to_dev(gpu, w["u0"], "f64"), tol=1e-8)

@@ -270,6 +270,52 @@ def test_2d_matvec_kron_and_gemm_forms_agree():
     np.testing.assert_allclose(P.apply_inverse(x), np.linalg.solve(P.dense(), x), atol=1e-12)
 
 
+def _var_problem_2d(n1, n2, seed=4):
+    rng = np.random.default_rng(seed)
+    return Problem2D(alpha=1.3, beta=1.8, n1=n1, n2=n2, c0=0.7, sr=2.5,
+                     dp=rng.uniform(1, 2, (n2, n1)), dm=rng.uniform(1, 2, (n2, n1)),
+                     ep=rng.uniform(1, 2, (n2, n1)), em=rng.uniform(1, 2, (n2, n1)))
+
+
+@pytest.mark.parametrize("n1,n2", [(7, 5), (15, 31)])
+def test_2d_matvec_entries_match_kronecker_matrix(n1, n2):
+    # every entry (y_j, x_i) of M x from the per-entry row sums against the
+    # explicit Kronecker-product matrix (Sec. 1.4), n1 != n2 so that a swapped
+    # axis or a transposed factor cannot cancel
+    prob = _var_problem_2d(n1, n2)
+    x = np.random.default_rng(9).standard_normal(n1 * n2)
+    rows, cols = np.divmod(np.arange(n1 * n2), n1)
+    got = prob.matvec_entries(x, rows, cols)
+    np.testing.assert_allclose(got, prob.dense() @ x, rtol=0, atol=1e-12 * np.max(np.abs(prob.dense() @ x)))
+
+
+@pytest.mark.parametrize("scheme", [GL1, WSGD2])
+@pytest.mark.parametrize("n", [1, 2, 7, 300, 1023])
+def test_1d_fft_convolution_path_matches_dense(n, scheme):
+    rng = np.random.default_rng(n)
+    prob = Problem1D(alpha=1.6, n=n, c0=0.1, dp=rng.uniform(1, 2, n), dm=rng.uniform(1, 2, n), scheme=scheme)
+    x = rng.standard_normal(n)
+    ref = prob.dense() @ x
+    np.testing.assert_allclose(prob.matvec(x, "fft"), ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
+
+
+def test_1d_fft_convolution_path_matches_direct_at_8191():
+    rng = np.random.default_rng(8)
+    n = 8191
+    prob = Problem1D(alpha=1.3, n=n, c0=0.01, dp=rng.uniform(1, 2, n), dm=rng.uniform(1, 2, n))
+    x = rng.standard_normal(n)
+    ref = prob.matvec(x, "direct")
+    np.testing.assert_allclose(prob.matvec(x, "fft"), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n1,n2", [(1, 1), (7, 5), (15, 31), (63, 127)])
+def test_2d_fft_convolution_path_matches_kronecker_and_gemm_forms(n1, n2):
+    prob = _var_problem_2d(n1, n2, seed=n1 + n2)
+    x = np.random.default_rng(n1 * n2).standard_normal(n1 * n2)
+    ref = prob.dense() @ x if n1 * n2 <= 1024 else prob.matvec(x)
+    np.testing.assert_allclose(prob.matvec(x, "fft"), ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
+
+
 def test_1d_direct_convolution_path_matches_dense():
     rng = np.random.default_rng(5)
     n = 300
@@ -462,6 +508,36 @@ def test_planted_index_shift_breaks_hankel_pin():
     S = sine_matrix(n)
     B = S @ (A - H) @ S
     assert np.max(np.abs(B - np.diag(np.diag(B)))) > 1e-3
+
+
+@pytest.mark.parametrize("plant", ["x_transposed", "y_transposed", "axes_swapped"])
+def test_planted_mistakes_break_matvec_entries_pin(plant):
+    # T^T for T on the x lines (Ta[i] <-> Ta[:, i]), the same on the y lines,
+    # or the coefficient arrays of the two axes exchanged: each changes entries
+    # of M x that the Kronecker matrix fixes
+    n1, n2 = 7, 5
+    prob = _var_problem_2d(n1, n2)
+    x = np.random.default_rng(9).standard_normal(n1 * n2)
+    U = x.reshape(n2, n1)
+    Ta, Tb = prob.Ta(), prob.Tb()
+    rows, cols = np.divmod(np.arange(n1 * n2), n1)
+    bad = np.empty(n1 * n2)
+    for t, (j, i) in enumerate(zip(rows, cols)):
+        if plant == "x_transposed":
+            ax = prob.dp[j, i] * (Ta[:, i] @ U[j]) + prob.dm[j, i] * (Ta[i] @ U[j])
+        else:
+            ax = prob.dp[j, i] * (Ta[i] @ U[j]) + prob.dm[j, i] * (Ta[:, i] @ U[j])
+        if plant == "y_transposed":
+            ay = prob.ep[j, i] * (Tb[:, j] @ U[:, i]) + prob.em[j, i] * (Tb[j] @ U[:, i])
+        else:
+            ay = prob.ep[j, i] * (Tb[j] @ U[:, i]) + prob.em[j, i] * (Tb[:, j] @ U[:, i])
+        if plant == "axes_swapped":
+            ax, ay = (prob.ep[j, i] * (Ta[i] @ U[j]) + prob.em[j, i] * (Ta[:, i] @ U[j]),
+                      prob.dp[j, i] * (Tb[j] @ U[:, i]) + prob.dm[j, i] * (Tb[:, j] @ U[:, i]))
+        bad[t] = prob.c0 * U[j, i] + ax + prob.sr * ay
+    ref = prob.dense() @ x
+    assert np.max(np.abs(bad - ref)) > 1e-3 * np.max(np.abs(ref))
+    np.testing.assert_allclose(prob.matvec_entries(x, rows, cols), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
 
 
 def test_planted_missing_shift_breaks_bounded_iterations():

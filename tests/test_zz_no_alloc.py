@@ -44,29 +44,41 @@ def test_rejects_invalid_arguments(L):
 def test_matches_plan_matvec_two_calls_in_a_row(gpu):
     import torch
 
+    import oracle
+
     # Rounding order differs (global-memory radix-8 passes against the
     # engine's shared-memory transforms); both are FP64 FFT products whose
-    # error is a few ulps times log2(L) relative to the largest entry.
+    # error is a few ulps times log2(L) relative to the largest entry.  The
+    # oracle's dense product from the weights is the reference of both.
     tol = 1e-12
     rng = np.random.default_rng(7)
     cases = []
     for n, alpha, weights, scheme, variable in [(4095, 1.7, "gl1", "ie", True), (255, 1.3, "wsgd2", "cn", False),
                                                 (1, 1.5, "gl1", "ie", True)]:
         h = 1.0 / (n + 1)
+        dt = 1.0 / 256
         xg = h * np.arange(1, n + 1)
         kw = dict(weights=weights, scheme=scheme)
         if variable:
-            kw.update(dp=1 + xg ** 2, dm=1 + (1 - xg) ** 2)
+            dp, dm = 1 + xg ** 2, 1 + (1 - xg) ** 2
+            kw.update(dp=dp, dm=dm)
         else:
+            dp = dm = np.full(n, 0.7)
             kw.update(dp_const=0.7, dm_const=0.7)
-        plan = fde.Plan(1, n, alpha, 1.0 / 256, **kw)
-        x = torch.tensor(rng.uniform(-1, 1, n), device="cuda", dtype=torch.float64)
-        cases.append((plan, x, plan.matvec(x)))
+        plan = fde.Plan(1, n, alpha, dt, **kw)
+        xh = rng.uniform(-1, 1, n)
+        x = torch.tensor(xh, device="cuda", dtype=torch.float64)
+        c0 = (2.0 if scheme == "cn" else 1.0) * h ** alpha / dt
+        prob = oracle.Problem1D(alpha=alpha, n=n, c0=c0, dp=dp, dm=dm, scheme=weights)
+        cases.append((plan, x, plan.matvec(x), prob.matvec(xh, "dense")))
     torch.cuda.synchronize()
     for rep in range(2):
-        for plan, x, ref in cases:
+        for plan, x, ref, ref_oracle in cases:
             y = torch.full_like(x, float("nan"))
             fde.toeplitz_matvec_noalloc(plan.problem, x, y)
             torch.cuda.synchronize()
             err = (y - ref).abs().max().item() / ref.abs().max().item()
             assert err < tol, (rep, plan.n1, err)
+            yh = y.cpu().numpy()
+            err_o = np.max(np.abs(yh - ref_oracle)) / np.max(np.abs(ref_oracle))
+            assert err_o < tol, (rep, plan.n1, err_o)
