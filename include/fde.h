@@ -115,6 +115,14 @@ typedef struct {
     int32_t restarts;      /* GMRES restarts */
     double relres;         /* final true ||b - A x||_2/||b||_2, FP64 */
     double relres_est;     /* the Krylov loop's own last residual estimate */
+    /* work counters, for accounting the bytes a solve moved: */
+    int32_t basis_sum;     /* sum over GMRES steps of the basis vectors the step orthogonalised against */
+    int32_t reorth;        /* GMRES steps that took a second Gram-Schmidt pass */
+    int32_t cycles;        /* Krylov cycles started from a true residual (restarts + 1 per Krylov solve) */
+    int32_t residuals64;   /* FP64 true residuals of the FP32 and refinement modes */
+    int32_t iterations64;  /* of `iterations`, those on FP64 vectors (all in FDE_PREC_F64; in
+                              FDE_PREC_F32_IR those of an FP64 finish) */
+    int32_t reserved;      /* 0 */
 } fde_solve_info;
 
 typedef struct fde_plan fde_plan;
@@ -261,6 +269,14 @@ fde_status fde_autotune(fde_plan* plan, void* stream, int* ctas, int* log_p1);
  * Asynchronous on `stream`.
  */
 fde_status fde_selftest_barrier_timeout(const fde_plan* plan, int* status_dev, void* stream);
+
+/*
+ * Measurement helper (no counterpart in the paper): the FP64 FMA rate of the
+ * current device in TFLOP/s, from one launch of eight independent DFMA
+ * chains per thread over every SM (the denominator of the FP64 rooflines).
+ * Synchronises `stream`; *tflops is host memory.
+ */
+fde_status fde_measure_fp64_rate(double* tflops, void* stream);
 
 /* Scalars the plan derived from the problem: c0, sr, h1^alpha. */
 fde_status fde_plan_scalars(const fde_plan* plan, double* c0, double* sr, double* h_alpha);

@@ -366,6 +366,7 @@ class Tau1D:
     F: np.ndarray
     D: Optional[np.ndarray] = None
     order: str = ORDER_TAU_D
+    fast: bool = False         # S through the library DST-I at every size (else the dense S up to n = 4096)
 
     @staticmethod
     def for_problem(prob: Problem1D, shift: bool = False, order: str = ORDER_TAU_D) -> "Tau1D":
@@ -389,7 +390,7 @@ class Tau1D:
 
     def tau_inv(self, r: np.ndarray) -> np.ndarray:
         n = len(self.F)
-        if n <= 4096:
+        if n <= 4096 and not self.fast:
             S = sine_matrix(n)
             return S @ ((S @ r) / self.F)
         return apply_sine_fast(apply_sine_fast(r) / self.F)
@@ -532,8 +533,10 @@ def gmres(A: Callable, b: np.ndarray, Pinv: Optional[Callable] = None, x0=None,
           maxiter: int = 10000) -> KrylovResult:
     """Restarted GMRES(m) with modified Gram-Schmidt Arnoldi and Givens rotations.
 
-    side="right": Krylov space of A P^-1; stops when the Arnoldi residual
-    estimate |g_{j+1}| <= tol ||b|| (the true residual norm in exact arithmetic).
+    side="right": Krylov space of A P^-1; a cycle ends when the Arnoldi
+    residual estimate |g_{j+1}| <= tol ||b|| (the true residual norm in exact
+    arithmetic), and the solve stops when the recomputed true residual
+    ||b - A x|| <= tol ||b||, else it restarts from that residual.
     side="left": Krylov space of P^-1 A; stops when ||P^-1 (b - A x)|| <=
     tol ||P^-1 (b - A x0)||, the convention the paper's experiments (Sec. 4)
     are reproduced with.
@@ -602,13 +605,17 @@ def gmres(A: Callable, b: np.ndarray, Pinv: Optional[Callable] = None, x0=None,
             y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
         u = V[:k].T @ y
         x += Pinv(u) if side == "right" else u
-        if converged or its >= maxiter:
+        if its >= maxiter or (converged and side == "left"):
             break
-        restarts += 1
+        # right preconditioning: the stopping test is on the true residual
+        # b - A x, recomputed after the cycle; where rounding has moved the
+        # Arnoldi estimate away from it, the solve restarts from it
         r = residual(x)
         beta = np.linalg.norm(r)
         if beta <= tol * ref:
             converged = True
             break
+        converged = False
+        restarts += 1
     relres = float(np.linalg.norm(b - A(x)) / nb)
     return KrylovResult(x, its, converged, relres, restarts, hist)

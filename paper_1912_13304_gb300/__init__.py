@@ -54,6 +54,8 @@ class FdeSolveInfo(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("outer", ctypes.c_int32),
         ("restarts", ctypes.c_int32), ("relres", ctypes.c_double), ("relres_est", ctypes.c_double),
+        ("basis_sum", ctypes.c_int32), ("reorth", ctypes.c_int32), ("cycles", ctypes.c_int32),
+        ("residuals64", ctypes.c_int32), ("iterations64", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -98,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.fde_krylov_solve.restype = cint
         L.fde_step_rhs.argtypes = [vp, vp, vp, vp, vp]
         L.fde_step_rhs.restype = cint
+        L.fde_measure_fp64_rate.argtypes = [P(cdbl), vp]
+        L.fde_measure_fp64_rate.restype = cint
         L.fde_plan_scalars.argtypes = [vp, P(cdbl), P(cdbl), P(cdbl)]
         L.fde_plan_scalars.restype = cint
         L.fde_plan_destroy.argtypes = [vp]
@@ -246,6 +250,13 @@ def plan_scalars(plan: int) -> tuple[float, float, float]:
     return c0.value, sr.value, ha.value
 
 
+def measure_fp64_rate(stream=None) -> float:
+    """FP64 FMA rate of the current device in TFLOP/s (fde_measure_fp64_rate)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().fde_measure_fp64_rate(ctypes.byref(v), _stream(stream)), "fde_measure_fp64_rate")
+    return v.value
+
+
 def plan_destroy(plan: int):
     if plan:
         lib().fde_plan_destroy(plan)
@@ -254,7 +265,8 @@ def plan_destroy(plan: int):
 def decode_info(raw: bytes, count: int) -> list[dict]:
     arr = (FdeSolveInfo * count).from_buffer_copy(raw)
     return [dict(status=a.status, iterations=a.iterations, outer=a.outer, restarts=a.restarts,
-                 relres=a.relres, relres_est=a.relres_est) for a in arr]
+                 relres=a.relres, relres_est=a.relres_est, basis_sum=a.basis_sum, reorth=a.reorth,
+                 cycles=a.cycles, residuals64=a.residuals64, iterations64=a.iterations64) for a in arr]
 
 
 from .solver import Plan, solve_batch  # noqa: E402,F401

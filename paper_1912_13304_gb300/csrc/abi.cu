@@ -1258,3 +1258,58 @@ extern "C" fde_status fde_selftest_barrier_timeout(const fde_plan* p, int* statu
     if (cudaMemsetAsync(p->sync_dev, 0, offsetof(SyncArea, partial), st) != cudaSuccess) return FDE_ECUDA;
     return FDE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// FP64 FMA rate probe: the denominator of the FP64 rooflines, measured
+// ---------------------------------------------------------------------------
+
+namespace {
+
+__device__ double g_dfma_sink;
+
+// Eight independent FMA chains per thread; the sum is stored only if it
+// equals a value it never reaches, which keeps the chains live.
+__global__ void __launch_bounds__(256) k_dfma_rate(int iters, double seed) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = seed + 1e-7 * (double)threadIdx.x + (double)k;
+    const double m = 1.0000000001, c = 1e-12;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == -1.0) g_dfma_sink = s;
+}
+
+}  // namespace
+
+extern "C" fde_status fde_measure_fp64_rate(double* tflops, void* stream) {
+    if (!tflops) return FDE_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FDE_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FDE_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int blocks = sms * 8, threads = 256, iters = 20000;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return FDE_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return FDE_ECUDA;
+    }
+    fde_status s = FDE_OK;
+    k_dfma_rate<<<blocks, threads, 0, st>>>(iters / 10, 1.0);       // warm-up
+    if (cudaEventRecord(e0, st) != cudaSuccess) s = FDE_ECUDA;
+    k_dfma_rate<<<blocks, threads, 0, st>>>(iters, 1.0);
+    if (s == FDE_OK && cudaGetLastError() != cudaSuccess) s = FDE_ECUDA;
+    if (s == FDE_OK && cudaEventRecord(e1, st) != cudaSuccess) s = FDE_ECUDA;
+    float ms = 0.0f;
+    if (s == FDE_OK && cudaEventSynchronize(e1) != cudaSuccess) s = FDE_ECUDA;
+    if (s == FDE_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s = FDE_ECUDA;
+    if (s == FDE_OK) *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+}

@@ -53,12 +53,15 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
     SolveState st{};
     st.status = FDE_ENOCONV;
     int outer = 0;
+    int res64 = 0;             // FP64 residuals of the refinement and FP32 modes
+    int its64 = 0;             // iterations on FP64 vectors (FP64 mode: all; refinement: an FP64 finish)
     const long long N = I.N;
     long long lo, hi;
     team_range(t, N, lo, hi);
     if constexpr (MODE == kModeF64) {
         SolveParams sp{a.tol, a.max_iters, a.side, 0};
         if (!krylov_core<double>(t, I, lm_f64(I), b, x, sp, st, ks, wk)) return false;
+        its64 = st.iterations;
     } else {
         float* rhs32 = reinterpret_cast<float*>(I.wvec) + extra_vec_offset<float>(I);
         float* sol32 = rhs32 + N;
@@ -79,6 +82,7 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
             if (!team_sync(t)) return false;
             double rn;
             if (!residual64(t, I, b, x, ks, wk, rn)) return false;
+            ++res64;
             st.relres = nb > 0.0 ? rn / nb : 0.0;
             if (st.status == FDE_OK && !(st.relres <= a.tol)) st.status = FDE_ENOCONV;
         } else {
@@ -88,6 +92,7 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
             while (true) {
                 double rn;
                 if (!residual64(t, I, b, x, ks, wk, rn)) return false;
+                ++res64;
                 st.relres = nb > 0.0 ? rn / nb : 0.0;
                 if (!finite(rn)) { status = FDE_ENONFINITE; break; }
                 if (rn <= a.tol * nb) { status = FDE_OK; break; }
@@ -101,8 +106,12 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
                     s64.iterations = st.iterations;
                     SolveParams sp{a.tol, a.max_iters, a.side, 0};
                     if (!krylov_core<double>(t, I, lm_f64(I), b, x, sp, s64, ks, wk)) return false;
+                    its64 = s64.iterations - st.iterations;
                     st.iterations = s64.iterations;
                     st.restarts += s64.restarts;
+                    st.basis_sum += s64.basis_sum;
+                    st.reorth += s64.reorth;
+                    st.cycles += s64.cycles;
                     st.relres = s64.relres;
                     st.relres_est = s64.relres_est;
                     status = s64.status;
@@ -126,6 +135,9 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
                 if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, in, ks, wk)) return false;
                 st.iterations = in.iterations;
                 st.restarts += in.restarts;
+                st.basis_sum += in.basis_sum;
+                st.reorth += in.reorth;
+                st.cycles += in.cycles;
                 st.relres_est = in.relres_est;
                 inner_status = in.status;
                 for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) x[i] = x[i] + rn * double(sol32[i]);
@@ -143,6 +155,12 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
         inf.restarts = st.restarts;
         inf.relres = st.relres;
         inf.relres_est = st.relres_est;
+        inf.basis_sum = st.basis_sum;
+        inf.reorth = st.reorth;
+        inf.cycles = st.cycles;
+        inf.residuals64 = res64;
+        inf.iterations64 = its64;
+        inf.reserved = 0;
         a.info[idx] = inf;
     }
     return true;

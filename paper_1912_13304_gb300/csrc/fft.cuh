@@ -115,11 +115,57 @@ FDE_D void dft8(cx<R>* v) {
     v[7] = e[3] - o3;
 }
 
+// a W_16^E (forward) or a W_16^-E (inverse), W_16 = exp(-2 pi i / 16), for the
+// exponents that the 4 x 4 split of a 16-point DFT needs.
+template <typename R, bool INV, int E>
+FDE_D cx<R> w16(cx<R> a) {
+    const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173), h = R(0.70710678118654752440);
+    R wr, wi;   // W_16^E = wr - i wi
+    if constexpr (E == 1) { wr = c1; wi = s1; }
+    else if constexpr (E == 2) { wr = h; wi = h; }
+    else if constexpr (E == 3) { wr = s1; wi = c1; }
+    else if constexpr (E == 6) { wr = -h; wi = h; }
+    else { wr = -c1; wi = -s1; }                    // E == 9
+    if (!INV) wi = -wi;
+    return mk(a.x * wr - a.y * wi, a.x * wi + a.y * wr);
+}
+
+// 16-point DFT as 4 x 4: DFT4 over n1 of x[4 n1 + n2] for each n2, twiddle
+// W_16^(n2 k1), DFT4 over n2 for each k1; output X[k1 + 4 k2] in natural order.
+template <typename R, bool INV>
+FDE_D void dft16(cx<R>* v) {
+    cx<R> y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        cx<R> t[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+        dft4<R, INV>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) y[k1][n2] = t[k1];
+    }
+    y[1][1] = w16<R, INV, 1>(y[1][1]);
+    y[1][2] = w16<R, INV, 2>(y[1][2]);
+    y[1][3] = w16<R, INV, 3>(y[1][3]);
+    y[2][1] = w16<R, INV, 2>(y[2][1]);
+    y[2][2] = rot_quarter<R, INV>(y[2][2]);
+    y[2][3] = w16<R, INV, 6>(y[2][3]);
+    y[3][1] = w16<R, INV, 3>(y[3][1]);
+    y[3][2] = w16<R, INV, 6>(y[3][2]);
+    y[3][3] = w16<R, INV, 9>(y[3][3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        cx<R> t[4] = {y[k1][0], y[k1][1], y[k1][2], y[k1][3]};
+        dft4<R, INV>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+}
+
 template <typename R, int RAD, bool INV>
 FDE_D void dft_reg(cx<R>* v) {
     if constexpr (RAD == 2) dft2<R, INV>(v[0], v[1]);
     else if constexpr (RAD == 4) dft4<R, INV>(v);
-    else dft8<R, INV>(v);
+    else if constexpr (RAD == 8) dft8<R, INV>(v);
+    else dft16<R, INV>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -133,7 +179,7 @@ template <typename R, int RAD, int EPT, bool INV>
 FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, int logNs, const Tw& tw,
                                  bool smem_tw) {
     constexpr int K = EPT / RAD;                // items per thread
-    constexpr int LR = RAD == 8 ? 3 : (RAD == 4 ? 2 : 1);
+    constexpr int LR = RAD == 16 ? 4 : (RAD == 8 ? 3 : (RAD == 4 ? 2 : 1));
     const int logItems = logP - LR;             // items per line = P / RAD
     const int total = nlines << logItems;
     const int Ns = 1 << logNs;
@@ -151,12 +197,44 @@ FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, 
 #pragma unroll
             for (int r = 0; r < RAD; ++r) v[t][r] = buf[pad(base + j + (r << logItems))];
             if (Ns > 1) {
+                if constexpr (RAD == 16) {
+                    // w^1, w^2, w^4, w^8 from the table, the other powers as
+                    // products of those (at most three roundings each), each
+                    // applied as soon as it is formed
+                    auto look = [&](int e) {
+                        const int idx = (e * k) << twsh;
+                        const cx<R> w = smem_tw ? tw_quarter<R>(tw, idx) : gtab[idx];
+                        return INV ? conj(w) : w;
+                    };
+                    const cx<R> w1 = look(1), w2 = look(2), w4 = look(4), w8 = look(8);
+                    cx<R>* x = v[t];
+                    x[1] = x[1] * w1;
+                    x[2] = x[2] * w2;
+                    x[4] = x[4] * w4;
+                    x[8] = x[8] * w8;
+                    x[9] = x[9] * (w1 * w8);
+                    x[10] = x[10] * (w2 * w8);
+                    x[12] = x[12] * (w4 * w8);
+                    const cx<R> w3 = w1 * w2;
+                    x[3] = x[3] * w3;
+                    x[11] = x[11] * (w3 * w8);
+                    const cx<R> w5 = w1 * w4;
+                    x[5] = x[5] * w5;
+                    x[13] = x[13] * (w5 * w8);
+                    const cx<R> w6 = w2 * w4;
+                    x[6] = x[6] * w6;
+                    x[14] = x[14] * (w6 * w8);
+                    const cx<R> w7 = w3 * w4;
+                    x[7] = x[7] * w7;
+                    x[15] = x[15] * (w7 * w8);
+                } else {
 #pragma unroll
-                for (int r = 1; r < RAD; ++r) {
-                    const int idx = (r * k) << twsh;
-                    cx<R> w = smem_tw ? tw_quarter<R>(tw, idx) : gtab[idx];
-                    if (INV) w = conj(w);
-                    v[t][r] = v[t][r] * w;
+                    for (int r = 1; r < RAD; ++r) {
+                        const int idx = (r * k) << twsh;
+                        cx<R> w = smem_tw ? tw_quarter<R>(tw, idx) : gtab[idx];
+                        if (INV) w = conj(w);
+                        v[t][r] = v[t][r] * w;
+                    }
                 }
             }
             dft_reg<R, RAD, INV>(v[t]);
@@ -188,30 +266,69 @@ FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, 
 // slower overall.
 template <typename R> constexpr int kFftItems = 1;
 
+// Radix schedule of a 2^logP-point FFT: log2 of each pass's radix, written to
+// lr[] (at most 8 passes); returns the number of passes.  FP64 takes radix-8
+// passes and one radix-4 or radix-2 remainder.  FP32 takes radix-16 passes
+// (twice the work between two CTA barriers, and the registers to hold it)
+// and makes the smallest radix as large as possible, since the widest pass
+// bounds the lines one call can take.
+FDE_HD int fft_schedule(int logP, int elem_bytes, int* lr) {
+    int n = 0;
+    if (elem_bytes == 8) {
+        int rem = logP;
+        while (rem >= 3) { lr[n++] = 3; rem -= 3; }
+        if (rem > 0) lr[n++] = rem;
+        return n;
+    }
+    const int n16 = logP / 4, r = logP % 4;
+    int k16 = n16;
+    if (r == 2 && n16 >= 1) k16 = n16 - 1;
+    if (r == 1) k16 = n16 >= 2 ? n16 - 2 : 0;
+    for (int i = 0; i < k16; ++i) lr[n++] = 4;
+    if (r == 3) lr[n++] = 3;
+    else if (r == 2) {
+        if (n16 >= 1) { lr[n++] = 3; lr[n++] = 3; } else lr[n++] = 2;
+    } else if (r == 1) {
+        if (n16 >= 2) { lr[n++] = 3; lr[n++] = 3; lr[n++] = 3; }
+        else if (n16 == 1) { lr[n++] = 3; lr[n++] = 2; }
+        else lr[n++] = 1;
+    }
+    return n;
+}
+
 template <typename R, bool INV>
 FDE_D void fft_inplace(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
     constexpr int K = kFftItems<R>;
     const bool smem_tw = logP <= tw.logT;
+    int lr[8];
+    const int np = fft_schedule(logP, (int)sizeof(R), lr);
     int logNs = 0;
-    int rem = logP;
-    while (rem >= 3) {
-        stockham_pass_inplace<R, 8, 8 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
-        logNs += 3;
-        rem -= 3;
+    for (int i = 0; i < np; ++i) {
+        if constexpr (sizeof(R) == 4) {
+            if (lr[i] == 4) {
+                stockham_pass_inplace<R, 16, 16 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+                logNs += 4;
+                continue;
+            }
+        }
+        if (lr[i] == 3) stockham_pass_inplace<R, 8, 8 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        else if (lr[i] == 2) stockham_pass_inplace<R, 4, 4 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        else stockham_pass_inplace<R, 2, 2 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        logNs += lr[i];
     }
-    if (rem == 2) stockham_pass_inplace<R, 4, 4 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
-    else if (rem == 1) stockham_pass_inplace<R, 2, 2 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
 }
 
-// Radix items per line of the widest pass (the last one, whose radix is the
-// smallest), and the lines one call of fft_inplace can take.
-FDE_HD int fft_items_per_line(int logP) {
-    const int r = logP % 3;
-    const int last = r == 0 ? 3 : r;
-    return logP >= last ? 1 << (logP - last) : 1;
+// Radix items per line of the widest pass (the one with the smallest radix),
+// and the lines one call of fft_inplace can take.
+FDE_HD int fft_items_per_line(int logP, int elem_bytes) {
+    int lr[8];
+    const int np = fft_schedule(logP, elem_bytes, lr);
+    int mn = 4;
+    for (int i = 0; i < np; ++i) mn = lr[i] < mn ? lr[i] : mn;
+    return np > 0 ? 1 << (logP - mn) : 1;
 }
 FDE_HD int fft_lines_per_call(int logP, int threads, int elem_bytes) {
-    return threads * (elem_bytes == 4 ? kFftItems<float> : kFftItems<double>) / fft_items_per_line(logP);
+    return threads * (elem_bytes == 4 ? kFftItems<float> : kFftItems<double>) / fft_items_per_line(logP, elem_bytes);
 }
 
 // FFT of nlines lines of 2^logP at stride lstride (flat index), in batches
@@ -220,8 +337,12 @@ FDE_HD int fft_lines_per_call(int logP, int threads, int elem_bytes) {
 // whenever more than one batch is needed.  A single line with more radix
 // items than kFftItems<R> per thread is not supported (callers split such
 // lines).
+//
+// Not inlined: the radix passes then get the whole register budget of the
+// thread instead of what the calling phase leaves (its live state is saved
+// once per call, not held across every pass).
 template <typename R, bool INV>
-FDE_D void fft_lines(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
+FDE_NI void fft_lines(cx<R>* buf, int logP, int nlines, int lstride, const Tw tw) {
     const int cap = fft_lines_per_call(logP, blockDim.x, (int)sizeof(R));
     for (int l0 = 0; l0 < nlines; l0 += cap) {
         const int nl = (nlines - l0) < cap ? (nlines - l0) : cap;

@@ -34,6 +34,12 @@ struct SolveState {
     int status;
     double relres_est;
     double relres;         // true residual of the last check, relative to ||rhs||
+    // work counters (fde_solve_info): sum over Arnoldi steps of the basis
+    // vectors each step orthogonalised against, second Gram-Schmidt passes,
+    // Krylov cycles started from a true residual
+    int basis_sum;
+    int reorth;
+    int cycles;
 };
 
 // Shared-memory scalars of one CTA (identical in every CTA of a team), and
@@ -438,6 +444,7 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
         if (!finite(beta)) { st.status = FDE_ENONFINITE; break; }
         if (beta <= sp.tol * nb) { st.status = FDE_OK; st.relres_est = beta / nb; break; }
         if (st.iterations >= sp.max_iters) { st.status = FDE_ENOCONV; break; }
+        st.cycles++;
         if (threadIdx.x == 0) {
             ks.vs[0] = 1.0 / beta;
             ks.g[0] = beta;
@@ -463,6 +470,7 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
             }
             if (!arnoldi_right<W>(t, I, lm, u, j + 1, v.V, v.z, v.w, v.tt, ks, wk)) return false;
             st.iterations++;
+            st.basis_sum += j + 1;
             trace_mark(t, 30);
             // Scalar work is done by thread 0 and broadcast through ks.sc: an
             // FP64 instruction repeated by every warp costs that many times
@@ -485,6 +493,7 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
             }
             __syncthreads();
             if (ks.sc[0] != 0.0) {
+                st.reorth++;
                 // reorthogonalise: w <- w - V h, then h2 = V^T w (V_j was stored
                 // by this step's first phase; the team barrier of the reduction
                 // made it visible)
@@ -596,6 +605,7 @@ FDE_NI bool gmres_left_core(const Team& t, const Inst& I, int lm, const W* rhs, 
         if (!finite(beta)) { st.status = FDE_ENONFINITE; break; }
         if (beta <= sp.tol * ref || beta == 0.0) { st.status = FDE_OK; st.relres_est = beta / ref; break; }
         if (st.iterations >= sp.max_iters) { st.status = FDE_ENOCONV; break; }
+        st.cycles++;
         if (threadIdx.x == 0) {
             ks.vs[0] = 1.0 / beta;
             ks.g[0] = beta;
@@ -608,6 +618,8 @@ FDE_NI bool gmres_left_core(const Team& t, const Inst& I, int lm, const W* rhs, 
             if (!op_matvec<W>(t, I, lm, v.V + (long long)j * N, W(ks.vs[j]), v.z, v.tt, wk)) return false;
             if (!op_tau<W>(t, I, lm, v.z, W(1), v.w, wk)) return false;
             st.iterations++;
+            st.basis_sum += j + 1;
+            st.reorth++;               // the left variant always takes two passes
             if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, false, ks)) return false;
             if (threadIdx.x <= j) {
                 ks.y[threadIdx.x] = ks.red[threadIdx.x];
@@ -726,6 +738,7 @@ FDE_NI bool pcg_core(const Team& t, const Inst& I, int lm, const W* rhs, W* sol,
         if (sqrt(rr) <= sp.tol * nb) { st.status = FDE_OK; break; }
         st.status = FDE_ENOCONV;
         if (pass >= kPcgPasses - 1 || st.iterations >= sp.max_iters) break;
+        st.cycles++;
         if (!op_tau<W>(t, I, lm, r, W(1), z, wk)) return false;
         {
             const W* a[1] = {r};

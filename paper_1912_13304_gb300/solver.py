@@ -79,6 +79,14 @@ class Plan:
                 kw.update(ep=w["ep"].reshape(-1), em=w["em"].reshape(-1))
         return cls(**kw)
 
+    def reassemble(self, stream=None):
+        """Rebuild the plan's symbol data in its workspace on the stream
+        (fde_assemble_symbol again with the same problem and options) and
+        replace the host plan; the schedule returns to the default."""
+        h = assemble_symbol(self.problem, self.opts, self._ws_ptr, self.nbytes, stream)
+        plan_destroy(self.handle)
+        self.handle = h
+
     # -- operators ---------------------------------------------------------
     def matvec(self, x, y=None, stream=None):
         torch = _torch()

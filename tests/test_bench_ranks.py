@@ -114,17 +114,16 @@ def test_batch_shards_cover_every_instance_once_and_balance_the_cost():
         assert max(loads) / (sum(costs) / world) < 1.01
 
 
-def test_all_cores_oracle_sample_runs_one_process_per_core():
-    """The all-cores CPU baseline: the oracle sample in spawned worker
-    processes at once (one BLAS thread each), every worker counted."""
+def test_cpu_baseline_times_the_oracle_at_one_and_all_threads():
+    """The CPU baseline: the oracle's own solve of the n = 1023 PCG system,
+    at one FFT thread and at two, reported as solves/s with the threads used."""
     sys.path.insert(0, ROOT)
     import bench
-    one = bench.oracle_sample(1023, cap=3)
-    assert one[1] == 3 and one[0] > 0
-    r = bench.all_cores_sample(1023, 5, timeout_s=120, cores=2)
-    assert r["cores"] == 2 and r["value"] > 0
-    # two workers at once deliver at most twice a single worker's rate
-    assert r["value"] <= 2.0 * 3 / (one[0] * 5) * 3
+    s = bench.cpu_sample("latency1d", 1, 500)
+    assert s["solves"] == 1 and 1 <= s["iterations"] < 20 and s["seconds"] > 0
+    r = bench.cpu_baseline("latency1d", float(s["iterations"]), 500, 2)
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["value"] > 0
+    assert r["all_cores"]["cores"] == 2 and r["all_cores"]["value"] > 0
 
 
 def test_algorithmic_flop_counts_match_the_hand_counts():
@@ -133,11 +132,35 @@ def test_algorithmic_flop_counts_match_the_hand_counts():
     about 2.0 GFLOP; 4095^2 GMRES about 10.9 GFLOP."""
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.algorithmic_per_iteration(65535, 8)[1] == pytest.approx(27.85e6, rel=1e-3)
-    pcg2d = bench.FFTS_PER_ITERATION["pcg"] * 2 * 2047 * bench.fft_flops(4096)
-    gmres2d = bench.FFTS_PER_ITERATION["gmres"] * 2 * 4095 * bench.fft_flops(8192)
-    assert pcg2d == pytest.approx(2.013e9, rel=1e-3)
-    assert gmres2d == pytest.approx(10.90e9, rel=1e-3)
-    r = bench.alu_roofline(gmres2d, 1000.0, bench.FP64_PEAK_TFLOPS)
-    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(gmres2d / 1e12)
+    g1 = bench.Geometry(1, 65535, 1, "gmres", True, 2)
+    assert g1.transform_flops() == pytest.approx(27.85e6, rel=1e-3)
+    assert bench.Geometry(2, 2047, 2047, "pcg", False, 0).transform_flops() == pytest.approx(2.013e9, rel=1e-3)
+    assert bench.Geometry(2, 4095, 4095, "gmres", True, 4).transform_flops() == pytest.approx(10.90e9, rel=1e-3)
+    r = bench.alu_roofline(10.90e9, 1000.0, bench.FP64_PEAK_TFLOPS)
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(10.90e9 / 1e12)
     assert bench.FP64_PEAK_TFLOPS == pytest.approx(1.25856)
+
+
+def test_algorithmic_byte_count_matches_an_enumeration_of_the_passes():
+    """One full GMRES(20) cycle on the 4095^2 plane (20 steps, D_N and four
+    coefficient arrays), counted vector pass by vector pass: forming V_j reads
+    w and j basis vectors and writes V_j; the tau solve reads V_j and D^-1 and
+    writes z; the matvec reads z and four coefficient arrays and writes w; the
+    dots read w and j + 1 basis vectors; the cycle's residual reads x, b and
+    the coefficient arrays and writes V_0, its norm reads V_0, the update reads
+    20 basis vectors, D^-1 and x and writes x."""
+    sys.path.insert(0, ROOT)
+    import bench
+    m = 20
+    passes = 0
+    for j in range(m):
+        if j >= 1:
+            passes += 1 + j + 1
+        passes += 3 + 6 + (j + 2)
+    passes += (1 + 1 + 4 + 1) + 1 + (m + 1 + 2)
+    N = 4095 * 4095
+    g = bench.Geometry(2, 4095, 4095, "gmres", True, 4)
+    info = dict(iterations=m, cycles=1, basis_sum=sum(j + 1 for j in range(m)), residuals64=0, iterations64=m)
+    assert bench.solve_bytes(info, g, 8) == pytest.approx(passes * 8 * N)
+    info32 = dict(info, iterations64=0)
+    assert bench.solve_bytes(info32, g, 4) == pytest.approx(passes * 4 * N)

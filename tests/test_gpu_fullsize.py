@@ -73,7 +73,7 @@ def test_config3_2047_pcg_phat_matches_oracle(gpu, config3, precision):
     if precision == "f64":
         assert abs(info["iterations"] - ref.iterations) <= 1, (info, ref.iterations)
     rr = relres(prob, b, info["x"].cpu().numpy())
-    assert rr <= 1.01e-8 and abs(rr - info["relres"]) <= 1e-2 * rr + 1e-14, (rr, info)
+    assert rr <= 1.01e-8 and abs(rr - info["relres"]) <= 1e-2 * rr + 1e-12, (rr, info)
     tol = 1e-13 if precision == "f64" else 1e-12
     info2 = plan.solve(to_dev(gpu, b, "f64"), tol=tol, max_iters=300, inner_tol=1e-4, max_outer=100)
     assert info2["status"] == fde.OK, info2
@@ -103,7 +103,9 @@ def test_config5_4095_gmres20_step_matches_oracle(gpu, config5, precision):
     if precision == "f64":
         assert abs(info["iterations"] - ref.iterations) <= 1, (info, ref.iterations)
     rr = relres(prob, b, info["x"].cpu().numpy())
-    assert rr <= 1.01e-8 and abs(rr - info["relres"]) <= 1e-2 * rr + 1e-14, (rr, info)
+    # two FP64 evaluations of the residual differ by rounding of order
+    # u ||M|| ||x|| / ||b||, about 1e-13 here
+    assert rr <= 1.01e-8 and abs(rr - info["relres"]) <= 1e-2 * rr + 1e-12, (rr, info)
     plan.close()
 
 

@@ -4,9 +4,9 @@ y = M x (fde_toeplitz_matvec) and z = P^{-1} r (fde_tau_solve), element by
 element, for 1D lines held by one CTA and lines split across CTAs, 2D planes,
 both precisions and every preconditioner variant.
 
-Tolerances (max-norm error relative to max |reference|): FP64 1e-11 for the
-matvec and 1e-10 for the tau solve (FFT rounding grows like u log2 L; the tau
-solve divides by symbol samples down to ~h^alpha); FP32 2e-5 and 5e-4.
+Tolerances (max-norm error relative to max |reference|): C u log2(L) per
+operator and precision, u the unit roundoff and L the transform length (see
+TOL_C below for the constants and how they were set).
 """
 
 import numpy as np
@@ -17,19 +17,30 @@ import paper_1912_13304_gb300 as fde
 
 pytestmark = pytest.mark.gpu
 
-# Unit roundoff of each precision and the constant C of the bound
-# C u log2(L): an L-point FFT's rounding error grows like u log2 L relative to
-# the largest entry.  For the tau solve the division by the symbol samples
-# amplifies the transform errors and the signal alike (both sit in the
-# smoothest sine modes), so the relative error keeps the same form.
+# Bound on the relative max-norm error of an operator application whose
+# transforms have L real points per line: C u log2(L), u the unit roundoff.
+# An L-point FFT's rounding error grows like u log2 L relative to the largest
+# entry; for the tau solve the division by the symbol samples amplifies the
+# transform errors and the signal alike (both sit in the smoothest sine
+# modes), so the relative error keeps that form.  The constants are about
+# four to eight times the largest ratio err / (u log2 L) measured on a GB300
+# over every size and variant below (FP32: 0.6 for the matvec, 1.3 for tau;
+# FP64 matvec: 3.7, where the dense FP64 reference itself carries that).  The
+# FP64 tau bound grows with L beyond 8192: its reference, the oracle's symbol
+# from the complex power (1 - e^{i theta})^alpha, loses relative accuracy
+# like 1/theta_1 ~ L at the smallest sample, which the tau solve weighs most
+# (measured ratios 77, 178, 461 at L = 2^14, 2^15, 2^17).
 UNIT = {"f64": 2.0 ** -53, "f32": 2.0 ** -24}
-TOL_C = {("mv", "f64"): 5300.0, ("tau", "f64"): 53000.0, ("mv", "f32"): 20.0, ("tau", "f32"): 490.0}
+TOL_C = {("mv", "f64"): 16.0, ("tau", "f64"): 64.0, ("mv", "f32"): 6.0, ("tau", "f32"): 10.0}
 
 
 def tol(op, dtype, L):
     """Bound on the relative max-norm error of one operator application whose
     transforms have L real points per line."""
-    return TOL_C[(op, dtype)] * UNIT[dtype] * max(np.log2(L), 1.0)
+    c = TOL_C[(op, dtype)]
+    if (op, dtype) == ("tau", "f64"):
+        c = max(c, L / 64.0)
+    return c * UNIT[dtype] * max(np.log2(L), 1.0)
 
 
 def L1(n):
@@ -89,7 +100,7 @@ def test_matvec_1d_weights_and_orders(gpu, weights, alpha):
     plan, prob = make_1d(gpu, n, "var", alpha=alpha, weights=weights)
     x = np.random.default_rng(3).uniform(-1, 1, n)
     y = plan.matvec(to_dev(gpu, x, "f64")).cpu().numpy()
-    assert rel_err(y, prob.matvec(x)) < 1e-11
+    assert rel_err(y, prob.matvec(x)) < tol("mv", "f64", L1(n))
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

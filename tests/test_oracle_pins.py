@@ -316,6 +316,17 @@ def test_2d_fft_convolution_path_matches_kronecker_and_gemm_forms(n1, n2):
     np.testing.assert_allclose(prob.matvec(x, "fft"), ref, rtol=0, atol=1e-13 * np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("n", [1, 7, 255])
+def test_tau1d_library_dst_path_matches_dense_sine(n):
+    rng = np.random.default_rng(n + 3)
+    prob = Problem1D(alpha=1.4, n=n, c0=0.2, dp=rng.uniform(1, 2, n), dm=rng.uniform(1, 2, n))
+    P = Tau1D.for_problem(prob)
+    r = rng.standard_normal(n)
+    ref = P.apply_inverse(r)
+    P.fast = True
+    np.testing.assert_allclose(P.apply_inverse(r), ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
 def test_1d_direct_convolution_path_matches_dense():
     rng = np.random.default_rng(5)
     n = 300
