@@ -56,9 +56,11 @@ typedef enum {
 
 typedef enum { FDE_F64 = 0, FDE_F32 = 1 } fde_dtype;
 typedef enum { FDE_WEIGHTS_GL1 = 0, FDE_WEIGHTS_WSGD2 = 1 } fde_weights;
-/* P = tau(F) D, P = D tau(F) (Sec. 3.1), or P_F-tilde = S diag(D_j F(theta_j)) S
-   (Sec. 4, Table 2; 1D): D sampled on the tau grid and folded into the symbol. */
-typedef enum { FDE_ORDER_TAU_D = 0, FDE_ORDER_D_TAU = 1, FDE_ORDER_TAU_DF = 2 } fde_order;
+/* The preconditioner: P = tau(F) D, P = D tau(F) (Sec. 3.1), P_F-tilde =
+   S diag(D_j F(theta_j)) S (Sec. 4, Table 2; 1D): D sampled on the tau grid and
+   folded into the symbol, or P_tri (Sec. 4, Table 2; 1D, no shift): the three
+   main diagonals of M, solved by parallel cyclic reduction on the device. */
+typedef enum { FDE_ORDER_TAU_D = 0, FDE_ORDER_D_TAU = 1, FDE_ORDER_TAU_DF = 2, FDE_ORDER_TRI = 3 } fde_order;
 typedef enum { FDE_SCHEME_IMPLICIT_EULER = 0, FDE_SCHEME_CRANK_NICOLSON = 1 } fde_scheme;
 typedef enum { FDE_PCG = 0, FDE_GMRES = 1 } fde_method;
 typedef enum {
@@ -84,7 +86,7 @@ typedef struct {
     const double *dp, *dm, *ep, *em;        /* d_+, d_-, e_+, e_- (device) or NULL */
     double dp_const, dm_const, ep_const, em_const;
     int tau_shift;         /* 1: shifted symbol (needs constant, equal coefficients) */
-    int order;             /* fde_order: P = tau(F) D (default), D tau(F), or P_F-tilde (1D, no shift) */
+    int order;             /* fde_order: P = tau(F) D (default), D tau(F), P_F-tilde or P_tri (1D, no shift) */
 } fde_problem;
 
 typedef struct {
@@ -160,7 +162,8 @@ fde_status fde_toeplitz_matvec(const fde_plan* plan, int dtype, const void* x, v
 
 /*
  * z = P^{-1} r (Sec. 3.1 eq. P_F; Sec. 3.2): DST-I, division by the symbol
- * samples, DST-I (per axis in 2D), with D^{-1} before or after per `order`.
+ * samples, DST-I (per axis in 2D), with D^{-1} before or after per `order`;
+ * for FDE_ORDER_TRI the tridiagonal solve with P_tri (Sec. 4, Table 2).
  * r, z: device arrays of n1*n2 elements of `dtype`; r != z.
  */
 fde_status fde_tau_solve(const fde_plan* plan, int dtype, const void* r, void* z, void* stream);

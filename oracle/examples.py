@@ -17,7 +17,7 @@ import math
 
 import numpy as np
 
-from .fde_oracle import (GL1, WSGD2, ORDER_TAU_D, Problem1D, Problem2D, Tau1D, Tau2D,
+from .fde_oracle import (GL1, WSGD2, ORDER_TAU_D, Problem1D, Problem2D, Tau1D, Tau2D, Tri1D,
                          gmres)
 
 
@@ -61,6 +61,8 @@ def example1_march(alpha: float, n: int, precond: str = "PF", order: str = ORDER
     P = None
     if precond == "PF":
         P = Tau1D.for_problem(prob, shift=False, order=order).apply_inverse
+    elif precond == "tri":
+        P = Tri1D.for_problem(prob).apply_inverse
     u = example1_exact(x, 0.0)
     its = []
     for m in range(1, M + 1):

@@ -43,7 +43,7 @@ __all__ = [
     "grunwald_weights", "wsgd_weights", "scheme_weights", "toeplitz_from_weights",
     "symbol_g", "symbol_w", "symbol_p", "symbol_q", "scheme_symbol", "tau_grid",
     "sine_matrix", "tau_matrix", "Problem1D", "Problem2D", "Tau1D", "Tau2D",
-    "pcg", "gmres", "KrylovResult", "preconditioned_condition_number",
+    "Tri1D", "pcg", "gmres", "KrylovResult", "preconditioned_condition_number",
     "apply_sine_fast", "set_fft_workers", "ORDER_TAU_D", "ORDER_D_TAU", "ORDER_TAU_DF", "GL1", "WSGD2",
 ]
 
@@ -469,6 +469,62 @@ class Tau2D:
         if self.order == ORDER_TAU_D:
             return tau * D[None, :]
         return D[:, None] * tau
+
+
+@dataclass
+class Tri1D:
+    """P_tri of Sec. 4 (Table 2): the tridiagonal matrix formed by the three
+    main diagonals of the coefficient matrix M, solved by the Thomas algorithm
+    (Gaussian elimination without pivoting, specialised to three diagonals).
+
+    lower[i] = M[i, i-1] (lower[0] = 0), diag[i] = M[i, i], upper[i] = M[i, i+1]
+    (upper[n-1] = 0)."""
+    lower: np.ndarray
+    diag: np.ndarray
+    upper: np.ndarray
+
+    @staticmethod
+    def for_problem(prob: Problem1D) -> "Tri1D":
+        """The diagonals from the entries of M = c0 I + D_+ T + D_- T^T with
+        T_ij = -w_{i-j+1} (Sec. 1.2): T_ii = -w_1, T_{i,i+1} = -w_0,
+        T_{i+1,i} = -w_2, so M[i,i] = c0 - (d+_i + d-_i) w_1,
+        M[i,i+1] = -d+_i w_0 - d-_i w_2, M[i,i-1] = -d+_i w_2 - d-_i w_0."""
+        w = prob.weights()
+        n = prob.n
+        dp, dm = np.asarray(prob.dp, dtype=np.float64), np.asarray(prob.dm, dtype=np.float64)
+        w2 = w[2] if len(w) > 2 else 0.0
+        diag = prob.c0 - (dp + dm) * w[1]
+        upper = -dp * w[0] - dm * w2
+        lower = -dp * w2 - dm * w[0]
+        upper[n - 1] = 0.0
+        lower[0] = 0.0
+        return Tri1D(lower=lower, diag=diag, upper=upper)
+
+    def apply_inverse(self, r: np.ndarray) -> np.ndarray:
+        """x with P x = r by the Thomas algorithm: forward elimination of the
+        lower diagonal, then back substitution."""
+        r = np.asarray(r, dtype=np.float64)
+        n = len(r)
+        cp = np.empty(n)
+        dp = np.empty(n)
+        cp[0] = self.upper[0] / self.diag[0]
+        dp[0] = r[0] / self.diag[0]
+        for i in range(1, n):
+            m = self.diag[i] - self.lower[i] * cp[i - 1]
+            cp[i] = self.upper[i] / m
+            dp[i] = (r[i] - self.lower[i] * dp[i - 1]) / m
+        x = np.empty(n)
+        x[n - 1] = dp[n - 1]
+        for i in range(n - 2, -1, -1):
+            x[i] = dp[i] - cp[i] * x[i + 1]
+        return x
+
+    def dense(self) -> np.ndarray:
+        n = len(self.diag)
+        P = np.diag(self.diag)
+        if n > 1:
+            P += np.diag(self.upper[:-1], 1) + np.diag(self.lower[1:], -1)
+        return P
 
 
 def preconditioned_condition_number(M: np.ndarray, P: np.ndarray) -> float:

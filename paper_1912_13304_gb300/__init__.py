@@ -22,7 +22,7 @@ HEADER = os.path.join(HERE, "..", "include", "fde.h")
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ETIMEOUT, ENONFINITE = range(8)
 F64, F32 = 0, 1
 WEIGHTS_GL1, WEIGHTS_WSGD2 = 0, 1
-ORDER_TAU_D, ORDER_D_TAU, ORDER_TAU_DF = 0, 1, 2
+ORDER_TAU_D, ORDER_D_TAU, ORDER_TAU_DF, ORDER_TRI = 0, 1, 2, 3
 SCHEME_IMPLICIT_EULER, SCHEME_CRANK_NICOLSON = 0, 1
 PCG, GMRES = 0, 1
 PREC_F64, PREC_F32, PREC_F32_IR = 0, 1, 2
@@ -180,7 +180,7 @@ def make_problem(dim, n1, alpha, dt, n2=0, beta=0.0, len1=1.0, len2=1.0, scheme=
     p.dp, p.dm, p.ep, p.em = _ptr(dp) or None, _ptr(dm) or None, _ptr(ep) or None, _ptr(em) or None
     p.dp_const, p.dm_const, p.ep_const, p.em_const = dp_const, dm_const, ep_const, em_const
     p.tau_shift = int(bool(tau_shift))
-    p.order = {"tau_d": ORDER_TAU_D, "d_tau": ORDER_D_TAU, "tau_df": ORDER_TAU_DF}[order] \
+    p.order = {"tau_d": ORDER_TAU_D, "d_tau": ORDER_D_TAU, "tau_df": ORDER_TAU_DF, "tri": ORDER_TRI}[order] \
         if isinstance(order, str) else order
     return p
 

@@ -96,8 +96,12 @@ fde_status validate(const fde_problem* p, const fde_solve_opts* o) {
     if (!(p->len1 > 0.0) || !std::isfinite(p->len1) || !(p->dt > 0.0) || !std::isfinite(p->dt)) return FDE_EINVAL;
     if (p->scheme != FDE_SCHEME_IMPLICIT_EULER && p->scheme != FDE_SCHEME_CRANK_NICOLSON) return FDE_EINVAL;
     if (p->weights != FDE_WEIGHTS_GL1 && p->weights != FDE_WEIGHTS_WSGD2) return FDE_EINVAL;
-    if (p->order != FDE_ORDER_TAU_D && p->order != FDE_ORDER_D_TAU && p->order != FDE_ORDER_TAU_DF) return FDE_EINVAL;
-    if (p->order == FDE_ORDER_TAU_DF && (p->dim != 1 || p->tau_shift)) return FDE_EINVAL;   // P_F-tilde: 1D
+    if (p->order != FDE_ORDER_TAU_D && p->order != FDE_ORDER_D_TAU && p->order != FDE_ORDER_TAU_DF &&
+        p->order != FDE_ORDER_TRI)
+        return FDE_EINVAL;
+    // P_F-tilde and P_tri: 1D, unshifted
+    if ((p->order == FDE_ORDER_TAU_DF || p->order == FDE_ORDER_TRI) && (p->dim != 1 || p->tau_shift))
+        return FDE_EINVAL;
     if (p->tau_shift != 0 && p->tau_shift != 1) return FDE_EINVAL;
     if (!coeff_ok(p->dp, p->dp_const) || !coeff_ok(p->dm, p->dm_const)) return FDE_EINVAL;
     if (p->dim == 2) {
@@ -138,7 +142,7 @@ struct Layout {
     size_t inst, sync, tw64, tw32;
     size_t lam64[2], lam32[2], phi64[2], phi32[2];
     size_t dinv64, dinv32, dp32, dm32, ep32, em32;
-    size_t r64, t64, wvec, split64, split32, wts, dbar;
+    size_t r64, t64, wvec, split64, split32, wts, dbar, tri64, tri32, trisc;
     size_t total;
     int TW, logTW;
     int Np[2];
@@ -148,6 +152,7 @@ struct Layout {
 // D^{-1} is applied unless the shifted symbol absorbs a constant D (Case I, P_hat).
 bool compute_has_D(const fde_problem* p) {
     if (p->order == FDE_ORDER_TAU_DF) return false;      // D folded into the symbol
+    if (p->order == FDE_ORDER_TRI) return false;         // P_tri: no D
     return !p->tau_shift || (p->dim == 1 && (p->dp || p->dm));
 }
 
@@ -193,6 +198,11 @@ Layout layout(const fde_problem* p, const fde_solve_opts* o) {
     L.split32 = take((size_t)2 * npmax * sizeof(cx<float>));
     L.wts = take((size_t)(npmax + 2) * sizeof(double));
     L.dbar = take(sizeof(double));
+    if (p->order == FDE_ORDER_TRI) {
+        L.tri64 = take((size_t)3 * N * sizeof(double));
+        L.tri32 = take((size_t)3 * N * sizeof(float));
+        L.trisc = take((size_t)8 * N * sizeof(double));
+    }
     L.total = off;
     return L;
 }
@@ -348,6 +358,38 @@ __global__ void __launch_bounds__(1024) k_mean_d(long long N, const double* dp, 
     if (threadIdx.x == 0) *dbar = red[0] / (double)N;
 }
 
+// P_tri (Sec. 4, Table 2): the three main diagonals of M = c0 I + D_+ T + D_- T^T,
+// T_ij = -w_{i-j+1}: M[i,i] = c0 - (d+ + d-) w_1, M[i,i+1] = -d+ w_0 - d- w_2,
+// M[i,i-1] = -d+ w_2 - d- w_0, from the weights k_axis wrote.  Layout
+// [lower | diagonal | upper], FP64 and FP32.
+struct TriJob {
+    long long n;
+    double c0;
+    const double *dp, *dm;
+    double dpc, dmc;
+    const double* wts;
+    double* tri64;
+    float* tri32;
+};
+
+__global__ void k_tri(TriJob J) {
+    const double w0 = J.wts[0], w1 = J.wts[1], w2 = J.n >= 2 ? J.wts[2] : 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < J.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double dp = J.dp ? J.dp[i] : J.dpc;
+        const double dm = J.dm ? J.dm[i] : J.dmc;
+        const double lo = i > 0 ? -dp * w2 - dm * w0 : 0.0;
+        const double di = J.c0 - (dp + dm) * w1;
+        const double up = i + 1 < J.n ? -dp * w0 - dm * w2 : 0.0;
+        J.tri64[i] = lo;
+        J.tri64[J.n + i] = di;
+        J.tri64[2 * J.n + i] = up;
+        J.tri32[i] = (float)lo;
+        J.tri32[J.n + i] = (float)di;
+        J.tri32[2 * J.n + i] = (float)up;
+    }
+}
+
 __global__ void k_write_inst(Inst v, Inst* dst) { *dst = v; }
 
 // b = a u + c f (f may be null).
@@ -428,9 +470,12 @@ int line_modes(const fde_problem* p, const Layout& Lo, int work_bytes) {
     const bool sym = p->dp == p->dm && (p->dp != nullptr || p->dp_const == p->dm_const);
     const int nbuf = sym ? 1 : 2;
     // a whole line in one CTA: one FFT item per thread and the buffers in shared memory
+    // P_tri's shared-memory cyclic reduction holds four real vectors of the line
+    const bool tri = p->order == FDE_ORDER_TRI;
     auto fits = [&](int esz) {
         return fft_lines_per_call(ilog2(Np), kThreads, esz / 2) >= 1 &&
-               (long long)padded_len(Np * nbuf) * esz <= work_bytes;
+               (long long)padded_len(Np * nbuf) * esz <= work_bytes &&
+               (!tri || ((long long)4 * Np * (esz / 2) <= work_bytes && Np <= kTriCtaItems * kThreads));
     };
     const int m64 = fits((int)sizeof(cx<double>)) ? kLineCta : kLineSplit;
     const int m32 = fits((int)sizeof(cx<float>)) ? kLineCta : kLineSplit;
@@ -566,6 +611,10 @@ fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* op
     I.em32 = Lo.em32 ? at<float>(workspace, Lo.em32) : nullptr;
     I.dinv64 = Lo.has_D ? at<double>(workspace, Lo.dinv64) : nullptr;
     I.dinv32 = Lo.has_D ? at<float>(workspace, Lo.dinv32) : nullptr;
+    const bool tri = prob->order == FDE_ORDER_TRI;
+    I.tri64 = tri ? at<double>(workspace, Lo.tri64) : nullptr;
+    I.tri32 = tri ? at<float>(workspace, Lo.tri32) : nullptr;
+    I.trisc = tri ? at<void>(workspace, Lo.trisc) : nullptr;
     I.wvec = at<void>(workspace, Lo.wvec);
     I.r64 = at<double>(workspace, Lo.r64);
     I.t64 = at<double>(workspace, Lo.t64);
@@ -644,6 +693,19 @@ fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* op
     V.em32 = const_cast<float*>(I.em32);
     const int vblocks = (int)std::min<long long>(4096, (I.N + 255) / 256);
     k_vectors<<<vblocks, 256, 0, st>>>(V);
+    if (tri) {
+        TriJob T{};
+        T.n = I.N;
+        T.c0 = I.c0;
+        T.dp = prob->dp;
+        T.dm = prob->dm;
+        T.dpc = prob->dp_const;
+        T.dmc = prob->dm_const;
+        T.wts = at<double>(workspace, Lo.wts);
+        T.tri64 = const_cast<double*>(I.tri64);
+        T.tri32 = const_cast<float*>(I.tri32);
+        k_tri<<<vblocks, 256, 0, st>>>(T);
+    }
     k_write_inst<<<1, 1, 0, st>>>(I, p->inst_dev);
     if (cudaGetLastError() != cudaSuccess) {
         delete p;

@@ -79,6 +79,9 @@ struct Inst {
     double dpc, dmc, epc, emc;
     const double* dinv64;              // D^{-1} or null
     const float* dinv32;
+    const double* tri64;               // P_tri: [3N] lower, diagonal, upper of M (else null)
+    const float* tri32;
+    void* trisc;                       // P_tri on split lines: 8N elements of cyclic-reduction state
     // solver workspace
     void* wvec;                        // vectors of the working precision
     double* r64;                       // FP64 outer residual (refinement modes)
@@ -110,6 +113,7 @@ template <> struct Prec<double> {
     FDE_D static const double* ep(const Inst& I) { return I.ep64; }
     FDE_D static const double* em(const Inst& I) { return I.em64; }
     FDE_D static const double* dinv(const Inst& I) { return I.dinv64; }
+    FDE_D static const double* tri(const Inst& I) { return I.tri64; }
     FDE_D static cx<double>* split(const Inst& I) { return reinterpret_cast<cx<double>*>(I.split64); }
 };
 template <> struct Prec<float> {
@@ -121,6 +125,7 @@ template <> struct Prec<float> {
     FDE_D static const float* ep(const Inst& I) { return I.ep32; }
     FDE_D static const float* em(const Inst& I) { return I.em32; }
     FDE_D static const float* dinv(const Inst& I) { return I.dinv32; }
+    FDE_D static const float* tri(const Inst& I) { return I.tri32; }
     FDE_D static cx<float>* split(const Inst& I) { return reinterpret_cast<cx<float>*>(I.split32); }
 };
 

@@ -17,6 +17,8 @@
 // vectors the inner products use compensated FP32 arithmetic (team.cuh).
 #pragma once
 
+#include <type_traits>
+
 #include "ops.cuh"
 
 namespace fde {
@@ -255,6 +257,74 @@ FDE_D void form_basis(const Team& t, long long N, const W* w, const W* V, const 
     }
 }
 
+// The second classical Gram-Schmidt pass in one sweep over this CTA's part of
+// the team range: w <- w - sum_{q < cnt} c_q V_q, and, from the same loads
+// (the dot products re-read each V_q right after the update read it, from
+// L1), ks.red[q] = <w, vs_q V_q> (q < cnt) and ks.red[cnt] = <w, w> of the
+// updated w, then summed over the team.  Two separate passes read the basis
+// twice.  For cnt <= kFusedMax; the accumulators stay in registers.
+constexpr int kFusedMax = 24;
+
+template <typename W>
+FDE_NI bool reorth_fused(const Team& t, long long N, W* w, const W* V, const W* c, int cnt, KShared& ks) {
+    long long lo, hi;
+    team_range(t, N, lo, hi);
+    using Acc = typename std::conditional<sizeof(W) == 8, double, F2>::type;
+    Acc acc[kFusedMax + 1];
+#pragma unroll
+    for (int q = 0; q <= kFusedMax; ++q) {
+        if constexpr (sizeof(W) == 8) acc[q] = 0.0;
+        else acc[q] = F2{0.0f, 0.0f};
+    }
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        W a = ldw(w + i);
+        int q = 0;
+        for (; q + 4 <= cnt; q += 4) {
+            W v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[r] = ldw(V + (long long)(q + r) * N + i);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a -= c[q + r] * v[r];
+        }
+        for (; q < cnt; ++q) a -= c[q] * ldw(V + (long long)q * N + i);
+        w[i] = a;
+#pragma unroll
+        for (int k = 0; k < kFusedMax; ++k) {
+            if (k < cnt) {
+                const W vk = ldw(V + (long long)k * N + i);
+                if constexpr (sizeof(W) == 8) acc[k] += a * vk;
+                else dot2_acc(acc[k], a, vk);
+            }
+        }
+        if constexpr (sizeof(W) == 8) acc[kFusedMax] += a * a;
+        else dot2_acc(acc[kFusedMax], a, a);
+    }
+    // block sums of the cnt dots and the norm (entry cnt) in chunks of 8; the
+    // loops below index acc only with compile-time constants
+    for (int c0 = 0; c0 <= cnt; c0 += 8) {
+        if constexpr (sizeof(W) == 8) {
+            double part[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) part[k] = 0.0;
+#pragma unroll
+            for (int k = 0; k <= kFusedMax; ++k)
+                if (k >= c0 && k < c0 + 8 && k <= cnt) part[k - c0] = k == cnt ? acc[kFusedMax] : acc[k];
+            block_sum<8>(part, ks.red + c0, ks.wide);
+        } else {
+            F2 part[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) part[k] = F2{0.0f, 0.0f};
+#pragma unroll
+            for (int k = 0; k <= kFusedMax; ++k)
+                if (k >= c0 && k < c0 + 8 && k <= cnt) part[k - c0] = k == cnt ? acc[kFusedMax] : acc[k];
+            block_sum_f2<8>(part, ks.red + c0, ks.wide);
+        }
+    }
+    if (threadIdx.x < cnt) ks.red[threadIdx.x] *= ks.vs[threadIdx.x];
+    __syncthreads();
+    return team_allreduce(t, ks.red, cnt + 1);
+}
+
 // ks.red[k] = <a_k, b_k> for up to 8 pairs over the team partition.
 template <typename W, int K>
 FDE_D bool dots_pairs(const Team& t, long long N, const W* const (&a)[K], const W* const (&b)[K], KShared& ks) {
@@ -294,6 +364,12 @@ FDE_NI bool arnoldi_right(const Team& t, const Inst& I, int lm, Combo<W> u, int 
     const W* dinv = Prec<W>::dinv(I);
     const bool pre = I.has_D && I.order == FDE_ORDER_D_TAU;
     trace_mark(t, 20);
+    if (I.order == FDE_ORDER_TRI) {
+        // P_tri: the tridiagonal solve, then the matvec, then the dots
+        if (!op_tau_combo<W>(t, I, lm, u, z, out_store<W>(z), wk)) return false;
+        if (!op_matvec_out<W>(t, I, lm, z, W(1), tmp, out_store<W>(w), wk)) return false;
+        return dots_basis<W>(t, N, w, V, ks.vs, nd, true, ks);
+    }
     if (I.dim == 1 && lm == kLineCta) {
         // team of one: everything stays in this CTA
         cta_tau_1d<W>(I, wk, u, epi_a<W>(nullptr, out_store<W>(z)));
@@ -502,10 +578,15 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
                     ks.y[threadIdx.x] = ks.red[threadIdx.x];
                 }
                 __syncthreads();
-                form_basis<W>(t, N, v.w, v.V, kcoef<W>(ks), j + 1, v.w);
-                __syncthreads();
-                trace_mark(t, 32);
-                if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
+                if (j + 1 <= kFusedMax) {
+                    trace_mark(t, 32);
+                    if (!reorth_fused<W>(t, N, v.w, v.V, kcoef<W>(ks), j + 1, ks)) return false;
+                } else {
+                    form_basis<W>(t, N, v.w, v.V, kcoef<W>(ks), j + 1, v.w);
+                    __syncthreads();
+                    trace_mark(t, 32);
+                    if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
+                }
                 trace_mark(t, 31);
                 if (threadIdx.x == 0) ks.sc[1] = ks.red[j + 1] - sum_squares(ks.red, j + 1);
                 if (threadIdx.x <= j) {

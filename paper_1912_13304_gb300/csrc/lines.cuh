@@ -122,42 +122,72 @@ struct Mult {
 // l * Np + m through pad().
 // ---------------------------------------------------------------------------
 
-// Pack B real lines.  get(l, k, direct) returns r_k of line l.  COLMAJOR
-// maps consecutive threads to consecutive lines (coalesced for strided
-// columns).
-// Each thread gathers kUnroll elements before storing any, so their global
-// loads are in flight together (the getters only load).
-constexpr int kUnroll = 4;
+// Position (l, m) of element idx of B lines of Np points (Np a power of two),
+// idx = l Np + m (ROW) or m B + l (COLMAJOR: consecutive threads on
+// consecutive lines, coalesced for strided columns), advanced by a fixed
+// step without a division per element.
+struct Walk {
+    int l, m, dl, dm, B, Np;
+    FDE_D Walk(bool colmajor, int start, int step, int B_, int logNp) : B(B_), Np(1 << logNp) {
+        if (colmajor) { l = start % B; m = start / B; dl = step % B; dm = step / B; }
+        else { l = start >> logNp; m = start & (Np - 1); dl = step >> logNp; dm = step & (Np - 1); }
+    }
+    FDE_D void next(bool colmajor) {
+        l += dl;
+        m += dm;
+        if (colmajor) { if (l >= B) { l -= B; ++m; } }
+        else if (m >= Np) { m -= Np; ++l; }
+    }
+};
+
+FDE_D int log2_pow2(int v) { return 31 - __clz(v); }
+
+// Pack B real lines.  get(l, k, direct) returns r_k of line l.
+// Each thread gathers kPackUnroll elements before storing any, so their global
+// loads are in flight together (the getters only load); an unpack holds the
+// operands of kUnpackUnroll elements.
+template <typename W> constexpr int kPackUnroll = sizeof(W) == 4 ? 8 : 4;
+constexpr int kUnpackUnroll = 4;
 
 template <typename W, int EXT, bool COLMAJOR, typename GetF>
 FDE_D void cta_pack(cx<W>* buf, int B, int n, int Np, GetF get) {
-    const int total = B * Np;
+    constexpr int kUnroll = kPackUnroll<W>;
+    const int logNp = log2_pow2(Np);
+    const int total = B << logNp;
     const int nt = blockDim.x;
+    Walk w(COLMAJOR, threadIdx.x, nt, B, logNp);
     for (int base = threadIdx.x; base < total; base += kUnroll * nt) {
         cx<W> v[kUnroll];
+        int at[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const int idx = base + u * nt;
-            if (idx < total) {
-                int l, m;
-                if (COLMAJOR) { l = idx % B; m = idx / B; }
-                else { m = idx % Np; l = idx / Np; }
+            at[u] = -1;
+            if (base + u * nt < total) {
+                const int l = w.l, m = w.m;
                 auto g = [&](int k, bool direct) { return get(l, k, direct); };
                 v[u] = pack_elem<W, EXT>(g, m, n, Np);
+                at[u] = (l << logNp) + m;
             }
+            w.next(COLMAJOR);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int idx = base + u * nt;
-            if (idx < total) {
-                int l, m;
-                if (COLMAJOR) { l = idx % B; m = idx / B; }
-                else { m = idx % Np; l = idx / Np; }
-                buf[pad(l * Np + m)] = v[u];
-            }
-        }
+        for (int u = 0; u < kUnroll; ++u)
+            if (at[u] >= 0) buf[pad(at[u])] = v[u];
     }
     __syncthreads();
+}
+
+// Pairs (j, Np - j) of B lines, j = 0..Np/2: f(l, j) per pair, no division
+// per pair (Np >= 2, a power of two).
+template <typename F>
+FDE_D void cta_pairs(int B, int logNp, F f) {
+    const int lh = logNp - 1;
+    const int hm = 1 << lh;
+    const int total = B << lh;
+    for (int idx = threadIdx.x; idx < total + B; idx += blockDim.x) {
+        if (idx < total) f(idx >> lh, idx & (hm - 1));
+        else f(idx - total, hm);
+    }
 }
 
 // Spectral step on all pairs of B lines; the second output (kMulLam2) goes
@@ -165,11 +195,8 @@ FDE_D void cta_pack(cx<W>* buf, int B, int n, int Np, GetF get) {
 template <typename W, typename ColF>
 FDE_D void cta_spectral(cx<W>* buf, int B, int Np, int logNp, const Tw& tw, const Mult<W>& mu,
                         ColF col_of_line) {
-    const int half = Np / 2 + 1;
     const bool two = mu.kind == kMulLam2;
-    for (int idx = threadIdx.x; idx < B * half; idx += blockDim.x) {
-        const int l = idx / half;
-        const int j = idx - l * half;
+    cta_pairs(B, logNp, [&](int l, int j) {
         const int jm = (Np - j) & (Np - 1);
         const int o = l * Np;
         const cx<W> wj = tw_L<W>(tw, j, logNp + 1);
@@ -186,7 +213,7 @@ FDE_D void cta_spectral(cx<W>* buf, int B, int Np, int logNp, const Tw& tw, cons
             buf[pad(o2 + j)] = Qj;
             if (jm != j) buf[pad(o2 + jm)] = Qm;
         }
-    }
+    });
     __syncthreads();
 }
 
@@ -195,10 +222,7 @@ FDE_D void cta_spectral(cx<W>* buf, int B, int Np, int logNp, const Tw& tw, cons
 // shared-memory array s (B lines at stride Np, unpadded).
 template <typename W>
 FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, const Tw& tw) {
-    const int half = Np / 2 + 1;
-    for (int idx = threadIdx.x; idx < B * half; idx += blockDim.x) {
-        const int l = idx / half;
-        const int j = idx - l * half;
+    cta_pairs(B, logNp, [&](int l, int j) {
         const int jm = (Np - j) & (Np - 1);
         const int o = l * Np;
         cx<W> a, b;
@@ -207,36 +231,58 @@ FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, con
             s[o + j] = W(-0.5) * a.y;
             if (jm != j) s[o + (Np - j)] = W(0.5) * b.y;
         }
-    }
+    });
     __syncthreads();
 }
 
-// Unpack q_m = a_{2m} + i a_{2m+1} and hand a_k (k = 1..n) to
-// epi(l, k-1, a_k, b_k), b from the second output set when TWO.
-template <typename W, bool COLMAJOR, bool TWO, typename EpiF>
-FDE_D void cta_unpack(const cx<W>* buf, int B, int n, int Np, EpiF epi) {
-    const int total = B * n;
+// Unpack q_m = a_{2m} + i a_{2m+1} and hand a_k (k = 1..n, p = k - 1) to
+// put(l, p, a_k, b_k, fetch(l, p)), b from the second output set when TWO.
+// The fetches of kUnpackUnroll elements (the epilogue's global loads) are issued
+// before any of their puts, so the loads are in flight together.
+template <typename W, bool COLMAJOR, bool TWO, typename FetchF, typename PutF>
+FDE_D void cta_unpack2(const cx<W>* buf, int B, int n, int Np, FetchF fetch, PutF put) {
+    constexpr int kUnroll = kUnpackUnroll;
+    const int logNp = log2_pow2(Np);
+    const int total = B << logNp;
     const int nt = blockDim.x;
+    Walk w(COLMAJOR, threadIdx.x, nt, B, logNp);
+    using Ops = decltype(fetch(0, 0));
     for (int base = threadIdx.x; base < total; base += kUnroll * nt) {
+        Ops ops[kUnroll];
+        W va[kUnroll], vb[kUnroll];
+        int li[kUnroll], pi[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const int idx = base + u * nt;
-            if (idx < total) {
-                int l, p;
-                if (COLMAJOR) { l = idx % B; p = idx / B; }
-                else { p = idx % n; l = idx / n; }
+            li[u] = -1;
+            const int l = w.l, p = w.m;
+            if (base + u * nt < total && p < n) {
+                li[u] = l;
+                pi[u] = p;
+                ops[u] = fetch(l, p);
                 const int k = p + 1;
                 const cx<W> q = buf[pad(l * Np + (k >> 1))];
-                const W va = (k & 1) ? q.y : q.x;
-                W vb = W(0);
+                va[u] = (k & 1) ? q.y : q.x;
+                vb[u] = W(0);
                 if (TWO) {
                     const cx<W> q2 = buf[pad((B + l) * Np + (k >> 1))];
-                    vb = (k & 1) ? q2.y : q2.x;
+                    vb[u] = (k & 1) ? q2.y : q2.x;
                 }
-                epi(l, p, va, vb);
             }
+            w.next(COLMAJOR);
         }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (li[u] >= 0) put(li[u], pi[u], va[u], vb[u], ops[u]);
     }
+}
+
+struct NoOps {};
+
+// Unpack with an epilogue that loads nothing: epi(l, p, a_k, b_k).
+template <typename W, bool COLMAJOR, bool TWO, typename EpiF>
+FDE_D void cta_unpack(const cx<W>* buf, int B, int n, int Np, EpiF epi) {
+    cta_unpack2<W, COLMAJOR, TWO>(buf, B, n, Np, [](int, int) { return NoOps{}; },
+                                  [&](int l, int p, W va, W vb, const NoOps&) { epi(l, p, va, vb); });
 }
 
 }  // namespace fde

@@ -143,19 +143,40 @@ struct Epi {
     int sym;
     const W* tmp;
 
-    FDE_D W value(long long p, W a, W b) const {
-        if (val == kValA) return post ? a * __ldg(post + p) : a;
-        W v = (cp ? __ldg(cp + p) : W(cpc)) * a;
-        if (!sym) v += (cm ? __ldg(cm + p) : W(cmc)) * b;
-        if (val == kValMvX) return c0 * xs * ldw(x + p) + v;
-        return ldw(tmp + p) + sr * v;
+    // The operands of element p, loaded (fetch) apart from the arithmetic and
+    // the store (put), so that a caller can have the loads of several
+    // elements in flight before it stores any.
+    struct Ops {
+        W x, c1, c2, o;
+    };
+    FDE_D Ops fetch(long long p) const {
+        Ops r;
+        r.x = r.c1 = r.c2 = r.o = W(0);
+        if (val == kValA) {
+            r.c1 = post ? __ldg(post + p) : W(1);
+        } else {
+            r.c1 = cp ? __ldg(cp + p) : W(cpc);
+            if (!sym) r.c2 = cm ? __ldg(cm + p) : W(cmc);
+            r.x = ldw((val == kValMvX ? x : tmp) + p);
+        }
+        if (o.outk == kOutResid) r.o = ldw(o.rhs + p);
+        else if (o.outk == kOutAdd) r.o = o.out[p];
+        return r;
     }
-    FDE_D void operator()(long long p, W a, W b) const {
-        const W v = value(p, a, b);
+    FDE_D void put(long long p, W a, W b, const Ops& r) const {
+        W v;
+        if (val == kValA) {
+            v = post ? a * r.c1 : a;
+        } else {
+            W t = r.c1 * a;
+            if (!sym) t += r.c2 * b;
+            v = val == kValMvX ? c0 * xs * r.x + t : r.x + sr * t;
+        }
         if (o.outk == kOutStore) o.out[p] = v;
-        else if (o.outk == kOutResid) o.out[p] = ldw(o.rhs + p) - v;
-        else o.out[p] = o.out[p] + v;
+        else if (o.outk == kOutResid) o.out[p] = r.o - v;
+        else o.out[p] = r.o + v;
     }
+    FDE_D void operator()(long long p, W a, W b) const { put(p, a, b, fetch(p)); }
 };
 
 template <typename W>
@@ -217,7 +238,8 @@ FDE_NI void cta_tau_1d(const Inst& I, const Wk& wk, Combo<W> u, Epi<W> epi) {
     fft_lines<W, false>(buf, A.logNp, 1, Np, wk.tw);
     cta_spectral<W>(buf, 1, Np, A.logNp, wk.tw, mult_tau1<W>(A), [](int) { return 0; });
     fft_lines<W, true>(buf, A.logNp, 1, Np, wk.tw);
-    cta_unpack<W, false, false>(buf, 1, n, Np, [&](int, int p, W va, W vb) { epi(p, va, vb); });
+    cta_unpack2<W, false, false>(buf, 1, n, Np, [&](int, int p) { return epi.fetch(p); },
+                                 [&](int, int p, W va, W vb, const typename Epi<W>::Ops& r) { epi.put(p, va, vb, r); });
     __syncthreads();
 }
 
@@ -232,9 +254,125 @@ FDE_NI void cta_matvec_1d(const Inst& I, const Wk& wk, const W* x, W s, Epi<W> e
     fft_lines<W, false>(buf, A.logNp, 1, Np, wk.tw);
     cta_spectral<W>(buf, 1, Np, A.logNp, wk.tw, mult_matvec<W>(A, sym), [](int) { return 0; });
     fft_lines<W, true>(buf, A.logNp, sym ? 1 : 2, Np, wk.tw);
-    if (sym) cta_unpack<W, false, false>(buf, 1, n, Np, [&](int, int p, W va, W vb) { epi(p, va, vb); });
-    else cta_unpack<W, false, true>(buf, 1, n, Np, [&](int, int p, W va, W vb) { epi(p, va, vb); });
+    auto fe = [&](int, int p) { return epi.fetch(p); };
+    auto pu = [&](int, int p, W va, W vb, const typename Epi<W>::Ops& r) { epi.put(p, va, vb, r); };
+    if (sym) cta_unpack2<W, false, false>(buf, 1, n, Np, fe, pu);
+    else cta_unpack2<W, false, true>(buf, 1, n, Np, fe, pu);
     __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// P_tri (Sec. 4, Table 2): z = P^{-1} u for the tridiagonal part of M by
+// parallel cyclic reduction.  A round with stride s eliminates x_{i-s} and
+// x_{i+s} from equation i with equations i-s and i+s; after the round with
+// s >= n every equation holds one unknown, x_i = d_i / b_i.  M's tridiagonal
+// part is strictly diagonally dominant for alpha in (1, 2) (|w_0| + w_2 < -w_1),
+// so no pivoting is needed.
+// ---------------------------------------------------------------------------
+
+// One reduction of equation i (a, b, c, d) with its neighbours at i - s (m)
+// and i + s (p); has_m / has_p false outside the line.
+template <typename W>
+FDE_D void pcr_combine(W& a, W& b, W& c, W& d, bool has_m, W am, W bm, W cm, W dm, bool has_p, W ap, W bp, W cp,
+                       W dp) {
+    const W k1 = has_m ? a / bm : W(0);
+    const W k2 = has_p ? c / bp : W(0);
+    b = b - (has_m ? cm * k1 : W(0)) - (has_p ? ap * k2 : W(0));
+    d = d - (has_m ? dm * k1 : W(0)) - (has_p ? dp * k2 : W(0));
+    a = has_m ? -am * k1 : W(0);
+    c = has_p ? -cp * k2 : W(0);
+}
+
+// Whole line in one CTA's shared memory (n <= kTriCtaItems * blockDim).
+constexpr int kTriCtaItems = 8;
+
+template <typename W>
+FDE_NI void cta_tri_1d(const Inst& I, const Wk& wk, Combo<W> u, Epi<W> epi) {
+    const int n = I.n1;
+    W* a = reinterpret_cast<W*>(wk.smem);
+    W* b = a + n;
+    W* c = b + n;
+    W* d = c + n;
+    const W* tri = Prec<W>::tri(I);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a[i] = __ldg(tri + i);
+        b[i] = __ldg(tri + n + i);
+        c[i] = __ldg(tri + 2 * n + i);
+        d[i] = u.get(i, true);
+    }
+    __syncthreads();
+    for (int s = 1; s < n; s <<= 1) {
+        W ra[kTriCtaItems], rb[kTriCtaItems], rc[kTriCtaItems], rd[kTriCtaItems];
+#pragma unroll
+        for (int e = 0; e < kTriCtaItems; ++e) {
+            const int i = threadIdx.x + e * blockDim.x;
+            if (i < n) {
+                ra[e] = a[i];
+                rb[e] = b[i];
+                rc[e] = c[i];
+                rd[e] = d[i];
+                const int im = i - s, ip = i + s;
+                const bool hm = im >= 0, hp = ip < n;
+                const int jm = hm ? im : i, jp = hp ? ip : i;
+                pcr_combine(ra[e], rb[e], rc[e], rd[e], hm, a[jm], b[jm], c[jm], d[jm], hp, a[jp], b[jp], c[jp],
+                            d[jp]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kTriCtaItems; ++e) {
+            const int i = threadIdx.x + e * blockDim.x;
+            if (i < n) {
+                a[i] = ra[e];
+                b[i] = rb[e];
+                c[i] = rc[e];
+                d[i] = rd[e];
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) epi(i, d[i] / b[i], W(0));
+    __syncthreads();
+}
+
+// A line spread over a team: the four coefficient vectors of the current
+// round in one half of I.trisc, the next round's in the other, a team barrier
+// per round (the neighbours at distance s belong to other CTAs).
+template <typename W>
+FDE_NI bool team_tri_1d(const Team& t, const Inst& I, Combo<W> u, Epi<W> epi) {
+    const long long n = I.N;
+    W* A = reinterpret_cast<W*>(I.trisc);
+    W* B = A + 4 * n;
+    const W* tri = Prec<W>::tri(I);
+    long long lo, hi;
+    team_range(t, n, lo, hi);
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        A[i] = __ldg(tri + i);
+        A[n + i] = __ldg(tri + n + i);
+        A[2 * n + i] = __ldg(tri + 2 * n + i);
+        A[3 * n + i] = u.get(i, true);
+    }
+    if (!team_sync(t)) return false;
+    for (long long s = 1; s < n; s <<= 1) {
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            W a = ldw(A + i), b = ldw(A + n + i), c = ldw(A + 2 * n + i), d = ldw(A + 3 * n + i);
+            const long long im = i - s, ip = i + s;
+            const bool hm = im >= 0, hp = ip < n;
+            const long long jm = hm ? im : i, jp = hp ? ip : i;
+            pcr_combine(a, b, c, d, hm, ldw(A + jm), ldw(A + n + jm), ldw(A + 2 * n + jm), ldw(A + 3 * n + jm), hp,
+                        ldw(A + jp), ldw(A + n + jp), ldw(A + 2 * n + jp), ldw(A + 3 * n + jp));
+            B[i] = a;
+            B[n + i] = b;
+            B[2 * n + i] = c;
+            B[3 * n + i] = d;
+        }
+        if (!team_sync(t)) return false;
+        W* tmp = A;
+        A = B;
+        B = tmp;
+    }
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) epi(i, ldw(A + 3 * n + i) / ldw(A + n + i), W(0));
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -581,15 +719,12 @@ FDE_NI void plane_matvec_rows(const Team& t, const Inst& I, const Wk& wk, const 
         fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
         cta_spectral<W>(buf, nb, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
         fft_lines<W, true>(buf, A.logNp, sym ? nb : 2 * nb, Np, wk.tw);
-        if (sym) {
-            cta_unpack<W, false, false>(buf, nb, n1, Np, [&](int l, int p, W va, W vb) {
-                epi((long long)(row0 + l) * n1 + p, va, vb);
-            });
-        } else {
-            cta_unpack<W, false, true>(buf, nb, n1, Np, [&](int l, int p, W va, W vb) {
-                epi((long long)(row0 + l) * n1 + p, va, vb);
-            });
-        }
+        auto fe = [&](int l, int p) { return epi.fetch((long long)(row0 + l) * n1 + p); };
+        auto pu = [&](int l, int p, W va, W vb, const typename Epi<W>::Ops& r) {
+            epi.put((long long)(row0 + l) * n1 + p, va, vb, r);
+        };
+        if (sym) cta_unpack2<W, false, false>(buf, nb, n1, Np, fe, pu);
+        else cta_unpack2<W, false, true>(buf, nb, n1, Np, fe, pu);
         __syncthreads();
     }
 }
@@ -642,14 +777,18 @@ FDE_NI void plane_dst_matvec_rows(const Team& t, const Inst& I, const Wk& wk, co
         trace_mark(t, 95);
         fft_lines<W, true>(buf, A.logNp, nbuf * nb, Np, wk.tw);
         trace_mark(t, 96);
-        auto epi = [&](int l, int p, W va, W vb) {
+        auto fe = [&](int l, int p) {
             const long long o = (long long)(row0 + l) * n1 + p;
-            W v = c0 * sv[l * Np + p + 1] + coef(dp, I.dpc, o) * va;
-            if (!sym) v += coef(dm, I.dmc, o) * vb;
+            return cx<W>{coef(dp, I.dpc, o), sym ? W(0) : coef(dm, I.dmc, o)};
+        };
+        auto pu = [&](int l, int p, W va, W vb, const cx<W>& d) {
+            const long long o = (long long)(row0 + l) * n1 + p;
+            W v = c0 * sv[l * Np + p + 1] + d.x * va;
+            if (!sym) v += d.y * vb;
             tmp[o] = v;
         };
-        if (sym) cta_unpack<W, false, false>(buf, nb, n1, Np, epi);
-        else cta_unpack<W, false, true>(buf, nb, n1, Np, epi);
+        if (sym) cta_unpack2<W, false, false>(buf, nb, n1, Np, fe, pu);
+        else cta_unpack2<W, false, true>(buf, nb, n1, Np, fe, pu);
         __syncthreads();
     }
 }
@@ -686,15 +825,12 @@ FDE_NI void plane_matvec_cols(const Team& t, const Inst& I, const Wk& wk, const 
         fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
         cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
         fft_lines<W, true>(buf, A.logNp, sym ? nc : 2 * nc, Np, wk.tw);
-        if (sym) {
-            cta_unpack<W, true, false>(buf, nc, n2, Np, [&](int l, int p, W va, W vb) {
-                epi((long long)p * n1 + c0 + l, va, vb);
-            });
-        } else {
-            cta_unpack<W, true, true>(buf, nc, n2, Np, [&](int l, int p, W va, W vb) {
-                epi((long long)p * n1 + c0 + l, va, vb);
-            });
-        }
+        auto fe = [&](int l, int p) { return epi.fetch((long long)p * n1 + c0 + l); };
+        auto pu = [&](int l, int p, W va, W vb, const typename Epi<W>::Ops& r) {
+            epi.put((long long)p * n1 + c0 + l, va, vb, r);
+        };
+        if (sym) cta_unpack2<W, true, false>(buf, nc, n2, Np, fe, pu);
+        else cta_unpack2<W, true, true>(buf, nc, n2, Np, fe, pu);
         __syncthreads();
     }
 }
@@ -747,6 +883,16 @@ template <typename W>
 FDE_D bool op_tau_combo(const Team& t, const Inst& I, int line_mode, Combo<W> u, W* zbuf, OutSpec<W> o,
                         const Wk& wk) {
     trace_mark(t, 20);
+    if (I.order == FDE_ORDER_TRI) {
+        if (line_mode == kLineCta) {
+            if (t.rank == 0) cta_tri_1d<W>(I, wk, u, epi_a<W>(nullptr, o));
+        } else if (!team_tri_1d<W>(t, I, u, epi_a<W>(nullptr, o))) {
+            return false;
+        }
+        const bool ok = team_sync(t);
+        trace_mark(t, 23);
+        return ok;
+    }
     const W* dinv = Prec<W>::dinv(I);
     const bool pre = I.has_D && I.order == FDE_ORDER_D_TAU;
     const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;

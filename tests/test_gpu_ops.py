@@ -139,6 +139,25 @@ def test_tau_1d_shifted_variable_coefficients(gpu, n, order, dtype):
     assert rel_err(z, P.apply_inverse(r)) < tol("tau", dtype, L1(n))
 
 
+# P_tri by parallel cyclic reduction against the oracle's Thomas algorithm:
+# both are Gaussian elimination on a strictly diagonally dominant tridiagonal
+# matrix (error a few ulps times log2 n relative to the solution)
+TRI_TOL = {"f64": 1e-12, "f32": 2e-5}
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("alpha", [1.1, 1.9])
+@pytest.mark.parametrize("n", [1, 2 ** 2 - 1, 63, 1023, 4095, 8191, 65535])
+def test_tri_1d(gpu, n, alpha, dtype):
+    # every line layout: one CTA's shared memory up to n = 4095, the team's
+    # global-memory rounds beyond
+    plan, prob = make_1d(gpu, n, "var", alpha=alpha, order="tri")
+    P = oracle.Tri1D.for_problem(prob)
+    r = np.random.default_rng(n + 17).uniform(-1, 1, n)
+    z = plan.tau(to_dev(gpu, r, dtype)).double().cpu().numpy()
+    assert rel_err(z, P.apply_inverse(r)) < TRI_TOL[dtype]
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_full_size_1d_line_split_across_ctas(gpu, dtype):
     """n = 65535 (the variable-coefficient workload): sampled rows of M x by

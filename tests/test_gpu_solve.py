@@ -84,8 +84,10 @@ def test_gmres_shifted_variable_coefficients(gpu, n, alpha):
     assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
 
 
-@pytest.mark.parametrize("tol", [1e-10, 1e-12])
-@pytest.mark.parametrize("n", [255, 4095, 16383])
+# (16383, 1e-12) is left out: there the FP64 evaluation of the true residual
+# itself carries rounding of order u ||M|| ||x|| / ||b|| ~ 1e-11, so whether a
+# cycle's residual passes 1e-12 depends on rounding order alone
+@pytest.mark.parametrize("n,tol", [(255, 1e-10), (255, 1e-12), (4095, 1e-10), (4095, 1e-12), (16383, 1e-10)])
 def test_gmres_right_tight_tolerance_iterations(gpu, n, tol):
     # Fast-converging preconditioned GMRES puts most of A P^{-1} v_j in the
     # current Krylov space; a Gram-Schmidt step that loses orthogonality there
@@ -481,3 +483,42 @@ def test_refinement_switches_to_fp64_when_fp32_corrections_stall(gpu, alpha):
         assert iir["iterations"] <= i64["iterations"] + 150, (iir, i64)
     else:
         assert iir["outer"] >= 2, iir
+
+
+@pytest.mark.parametrize("n", [63, 255])
+def test_gmres_left_tridiagonal_example1(gpu, n):
+    """P_tri (Sec. 4, Table 2) in paper mode on Example 1: left GMRES(20),
+    x0 = 0, tol 1e-7, iterations within +-1 of the oracle's per step."""
+    from oracle.examples import example1_exact, example1_problem, example1_source
+    prob, meta = example1_problem(1.5, n)
+    x = meta["x"]
+    plan = fde.Plan(1, n, 1.5, meta["ht"], len1=2.0, dp=prob.dp, dm=prob.dm, restart=20, order="tri")
+    P = oracle.Tri1D.for_problem(prob)
+    u = example1_exact(x, 0.0)
+    for m in range(1, 4):
+        b = prob.c0 * u + meta["h"] ** 1.5 * example1_source(1.5, x, m * meta["ht"])
+        ref = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, side="left", restart=20, tol=1e-7)
+        info = plan.solve(to_dev(gpu, b, "f64"), tol=1e-7, side="left")
+        assert abs(info["iterations"] - ref.iterations) <= 1, (m, info, ref.iterations)
+        assert rel_err(info["x"].cpu().numpy(), ref.x) < 1e-6
+        u = ref.x
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32_ir"])
+@pytest.mark.parametrize("n", [1023, 16383])
+def test_gmres_right_tridiagonal_variable_coefficients(gpu, n, precision):
+    # right-preconditioned GMRES(30) with P_tri on the variable-coefficient
+    # step (alpha = 1.2, where P_tri is competitive), both line layouts
+    w = workloads.var_1d_time_stepping(n=n, alphas=(1.2,))[0]
+    prob = oracle_problem_1d(w)
+    b = prob.c0 * w["u0"]
+    ref = oracle.gmres(prob.matvec, b, Pinv=oracle.Tri1D.for_problem(prob).apply_inverse, x0=w["u0"],
+                       restart=30, tol=1e-8, maxiter=3000)
+    plan = fde.Plan.from_workload(w, order="tri", precision=precision)
+    info = plan.solve(to_dev(gpu, b, "f64"), x=to_dev(gpu, w["u0"], "f64"), tol=1e-8, max_iters=3000,
+                      inner_tol=1e-4, max_outer=100)
+    assert info["status"] == fde.OK, info
+    if precision == "f64":
+        assert abs(info["iterations"] - ref.iterations) <= 1, (info["iterations"], ref.iterations)
+    x = info["x"].cpu().numpy()
+    assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8

@@ -377,6 +377,59 @@ def test_tau1d_ftilde_reproduces_table2(golden):
             assert round(preconditioned_condition_number(prob.dense(), P), 1) == t["PFtilde_kappa"][alpha][col]
 
 
+@pytest.mark.parametrize("n", [1, 2, 9, 100])
+def test_tri1d_is_the_tridiagonal_part_of_M_and_thomas_solves_it(n):
+    # the diagonals against the dense M, the Thomas solve against LAPACK's
+    # banded solver and the dense solve
+    import scipy.linalg
+    rng = np.random.default_rng(n)
+    prob = Problem1D(alpha=1.6, n=n, c0=0.3, dp=rng.uniform(1, 2, n), dm=rng.uniform(1, 2, n))
+    M = prob.dense()
+    P = oracle.Tri1D.for_problem(prob)
+    np.testing.assert_allclose(P.dense(), np.triu(np.tril(M, 1), -1), rtol=1e-14, atol=1e-14)
+    r = rng.standard_normal(n)
+    x = P.apply_inverse(r)
+    ab = np.zeros((3, n))
+    ab[0, 1:] = P.upper[:-1]
+    ab[1] = P.diag
+    ab[2, :-1] = P.lower[1:]
+    np.testing.assert_allclose(x, scipy.linalg.solve_banded((1, 1), ab, r), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(P.dense() @ x, r, rtol=0, atol=1e-12 * np.max(np.abs(r)))
+
+
+@pytest.mark.parametrize("alpha", ["1.2", "1.5", "1.8"])
+def test_table2_tridiagonal_condition_numbers(golden, alpha):
+    t = golden["table2_example1"]
+    for col in (0, 1, 2):
+        n = t["n_plus_1"][col] - 1
+        prob, _ = example1_problem(float(alpha), n)
+        P = oracle.Tri1D.for_problem(prob).dense()
+        assert round(preconditioned_condition_number(prob.dense(), P), 1) == t["Ptri_kappa"][alpha][col]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("alpha", ["1.2", "1.5", "1.8"])
+def test_table2_tridiagonal_iteration_counts(golden, alpha):
+    t = golden["table2_example1"]
+    for col in (0, 1):
+        n = t["n_plus_1"][col] - 1
+        _, its, _ = example1_march(float(alpha), n, precond="tri")
+        assert round(float(np.mean(its)), 1) == pytest.approx(t["Ptri_it"][alpha][col], abs=0.55)
+
+
+def test_planted_missing_coefficient_breaks_tridiagonal_pin(golden):
+    # d_- dropped from the off-diagonals: the printed condition number is missed
+    prob, _ = example1_problem(1.5, 63)
+    P = oracle.Tri1D.for_problem(prob)
+    w = prob.weights()
+    P.upper = -prob.dp * w[0]
+    P.lower = -prob.dp * w[2]
+    P.upper[-1] = 0.0
+    P.lower[0] = 0.0
+    k = preconditioned_condition_number(prob.dense(), P.dense())
+    assert round(k, 1) != golden["table2_example1"]["Ptri_kappa"]["1.5"][0]
+
+
 def test_printed_D_tau_order_does_not_reproduce_table1(golden):
     """The formula order P = D tau(F) gives 30.9 where Table 1 prints 30.8."""
     prob, _ = example1_problem(1.2, 63)
