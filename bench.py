@@ -662,6 +662,9 @@ def section_latency1d(args, device, world):
     xs = {}
     for prec in [p for p in args.precisions.split(",") if p]:
         plan = fde.Plan.from_workload(w, precision=prec, device=device)
+        # the autotuner picks between one CTA per line and a line split over a
+        # team of CTAs (at FP64 one SM's pipe makes the single-CTA line slow)
+        schedule = plan.autotune()
         b = plan.c0 * torch.tensor(w["b"], dtype=torch.float64, device=device)
         x = torch.zeros_like(b)
         info = torch.zeros(fde.INFO_BYTES, dtype=torch.uint8, device=device)
@@ -683,6 +686,7 @@ def section_latency1d(args, device, world):
         inf = fde.decode_info(info.cpu().numpy().tobytes(), 1)[0]
         s = _summary([inf])
         rec = dict(us_per_solve=1e3 * t, solves_per_s=1.0 / (t * 1e-3), **s,
+                   schedule={"ctas": schedule[0], "log_p1": schedule[1]},
                    unknown_iters_per_s=w["n1"] * inf["iterations"] / (t * 1e-3),
                    algorithmic_bytes_per_solve=solve_bytes(inf, g, 8 if prec == "f64" else 4))
         # the working set (~100 KB) lives in one SM's shared memory and L1: a

@@ -254,15 +254,35 @@ __device__ double symbol_sample(double a, int weights, int j, int Np) {
 __global__ void __launch_bounds__(1024) k_axis(AxisJob J) {
     const int n = J.n, Np = J.Np;
     const int L = 2 * Np;
-    if (threadIdx.x == 0) {
-        // weights w_0..w_{n+1}: g_k = (-1)^k binom(alpha, k) by the running product,
-        // WSGD w_k = (alpha/2) g_k + ((2-alpha)/2) g_{k-1}
-        double gprev = 1.0;
-        J.wts[0] = J.weights == FDE_WEIGHTS_GL1 ? 1.0 : 0.5 * J.alpha;
-        for (int k = 1; k <= n + 1; ++k) {
-            const double g = gprev * (-(J.alpha - k + 1.0) / k);
-            J.wts[k] = J.weights == FDE_WEIGHTS_GL1 ? g : 0.5 * J.alpha * g + 0.5 * (2.0 - J.alpha) * gprev;
-            gprev = g;
+    {
+        // weights w_0..w_{n+1}: g_k = (-1)^k binom(alpha, k) = f_1 f_2 ... f_k with
+        // f_i = -(alpha - i + 1) / i, as a parallel prefix product: each thread
+        // multiplies the factors of its chunk of k, a block scan gives each
+        // thread the product of all earlier chunks, and the thread then forms
+        // its g_k in order.  WSGD: w_k = (alpha/2) g_k + ((2-alpha)/2) g_{k-1}.
+        __shared__ double scan[1024];
+        const int K = n + 1;
+        const int nt = blockDim.x;
+        const int c = (K + nt - 1) / nt;
+        const int k0 = (int)threadIdx.x * c + 1;
+        const int k1 = k0 + c - 1 < K ? k0 + c - 1 : K;
+        double p = 1.0;
+        for (int k = k0; k <= k1; ++k) p *= -(J.alpha - k + 1.0) / k;
+        scan[threadIdx.x] = p;
+        __syncthreads();
+        for (int off = 1; off < nt; off <<= 1) {
+            const double v = (int)threadIdx.x >= off ? scan[threadIdx.x - off] : 1.0;
+            __syncthreads();
+            scan[threadIdx.x] *= v;
+            __syncthreads();
+        }
+        double g = threadIdx.x > 0 ? scan[threadIdx.x - 1] : 1.0;     // g_{k0 - 1}
+        const bool gl1 = J.weights == FDE_WEIGHTS_GL1;
+        if (threadIdx.x == 0) J.wts[0] = gl1 ? 1.0 : 0.5 * J.alpha;
+        for (int k = k0; k <= k1; ++k) {
+            const double gprev = g;
+            g *= -(J.alpha - k + 1.0) / k;
+            J.wts[k] = gl1 ? g : 0.5 * J.alpha * g + 0.5 * (2.0 - J.alpha) * gprev;
         }
     }
     __syncthreads();

@@ -259,11 +259,11 @@ FDE_D void form_basis(const Team& t, long long N, const W* w, const W* V, const 
 
 // The second classical Gram-Schmidt pass in one sweep over this CTA's part of
 // the team range: w <- w - sum_{q < cnt} c_q V_q, and, from the same loads
-// (the dot products re-read each V_q right after the update read it, from
-// L1), ks.red[q] = <w, vs_q V_q> (q < cnt) and ks.red[cnt] = <w, w> of the
-// updated w, then summed over the team.  Two separate passes read the basis
-// twice.  For cnt <= kFusedMax; the accumulators stay in registers.
-constexpr int kFusedMax = 24;
+// held in registers, ks.red[q] = <w, vs_q V_q> (q < cnt) and ks.red[cnt] =
+// <w, w> of the updated w, then summed over the team.  Two separate passes
+// read the basis twice.  For cnt <= kFusedMax; the basis values and the
+// accumulators stay in registers.
+constexpr int kFusedMax = 20;
 
 template <typename W>
 FDE_NI bool reorth_fused(const Team& t, long long N, W* w, const W* V, const W* c, int cnt, KShared& ks) {
@@ -277,23 +277,21 @@ FDE_NI bool reorth_fused(const Team& t, long long N, W* w, const W* V, const W* 
         else acc[q] = F2{0.0f, 0.0f};
     }
     for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        // every basis value of element i loaded once, into registers (static
+        // indices under predicates), for both the update and the dots
+        W v[kFusedMax];
+#pragma unroll
+        for (int k = 0; k < kFusedMax; ++k) v[k] = k < cnt ? ldw(V + (long long)k * N + i) : W(0);
         W a = ldw(w + i);
-        int q = 0;
-        for (; q + 4 <= cnt; q += 4) {
-            W v[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) v[r] = ldw(V + (long long)(q + r) * N + i);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) a -= c[q + r] * v[r];
-        }
-        for (; q < cnt; ++q) a -= c[q] * ldw(V + (long long)q * N + i);
+        for (int k = 0; k < kFusedMax; ++k)
+            if (k < cnt) a -= c[k] * v[k];
         w[i] = a;
 #pragma unroll
         for (int k = 0; k < kFusedMax; ++k) {
             if (k < cnt) {
-                const W vk = ldw(V + (long long)k * N + i);
-                if constexpr (sizeof(W) == 8) acc[k] += a * vk;
-                else dot2_acc(acc[k], a, vk);
+                if constexpr (sizeof(W) == 8) acc[k] += a * v[k];
+                else dot2_acc(acc[k], a, v[k]);
             }
         }
         if constexpr (sizeof(W) == 8) acc[kFusedMax] += a * a;

@@ -662,7 +662,9 @@ FDE_NI void plane_dst_rows(const Team& t, const Inst& I, const Wk& wk, Combo<W> 
         });
         trace_mark(t, 70);
         fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
+        trace_mark(t, 86);
         cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
+        trace_mark(t, 87);
         for (int idx = threadIdx.x; idx < nb * n1; idx += blockDim.x) {
             const int l = idx / n1, p = idx - l * n1;
             const long long o = (long long)(row0 + l) * n1 + p;
@@ -691,8 +693,11 @@ FDE_NI void plane_tau_cols(const Team& t, const Inst& I, const Wk& wk, W* z) {
         });
         trace_mark(t, 72);
         fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
+        trace_mark(t, 80);
         cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [&](int l) { return c0 + l; });
+        trace_mark(t, 81);
         fft_lines<W, true>(buf, A.logNp, nc, Np, wk.tw);
+        trace_mark(t, 82);
         cta_unpack<W, true, false>(buf, nc, n2, Np, [&](int l, int p, W va, W) {
             z[(long long)p * n1 + c0 + l] = va;
         });
@@ -823,8 +828,11 @@ FDE_NI void plane_matvec_cols(const Team& t, const Inst& I, const Wk& wk, const 
         });
         trace_mark(t, 76);
         fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
+        trace_mark(t, 83);
         cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
+        trace_mark(t, 84);
         fft_lines<W, true>(buf, A.logNp, sym ? nc : 2 * nc, Np, wk.tw);
+        trace_mark(t, 85);
         auto fe = [&](int l, int p) { return epi.fetch((long long)p * n1 + c0 + l); };
         auto pu = [&](int l, int p, W va, W vb, const typename Epi<W>::Ops& r) {
             epi.put((long long)p * n1 + c0 + l, va, vb, r);

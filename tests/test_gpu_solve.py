@@ -61,8 +61,11 @@ def test_gmres_right_variable_coefficients(gpu, n, alpha):
     assert abs(info["iterations"] - ref.iterations) <= 1, (info, ref.iterations)
     x = info["x"].cpu().numpy()
     assert np.linalg.norm(b - prob.matvec(x)) / np.linalg.norm(b) <= 1.01e-8
-    tight = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, restart=30, tol=1e-12, maxiter=3000)
-    info2 = plan.solve(to_dev(gpu, b, "f64"), tol=1e-12, max_iters=3000)
+    # 1e-12 lies below the FP64 residual floor at alpha = 1.8 (kappa(M) ~ 1e6):
+    # the reference stops on its Arnoldi estimate, the device on its iteration cap
+    tight = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, restart=30, tol=1e-12, maxiter=3000,
+                         stop_on_estimate=True)
+    info2 = plan.solve(to_dev(gpu, b, "f64"), tol=1e-12, max_iters=600)
     assert rel_err(info2["x"].cpu().numpy(), tight.x) < 1e-8
 
 
@@ -116,7 +119,8 @@ def test_gmres_refinement_fp32_inner(gpu, alpha):
     prob = oracle_problem_1d(w)
     b = prob.c0 * w["u0"]
     P = oracle.Tau1D.for_problem(prob)
-    tight = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, restart=30, tol=1e-12, maxiter=3000)
+    tight = oracle.gmres(prob.matvec, b, Pinv=P.apply_inverse, restart=30, tol=1e-12, maxiter=3000,
+                         stop_on_estimate=True)
     plan = fde.Plan.from_workload(w, precision="f32_ir")
     info = plan.solve(to_dev(gpu, b, "f64"), tol=1e-8, inner_tol=1e-3, max_iters=20000, max_outer=200)
     x = info["x"].cpu().numpy()
