@@ -53,7 +53,7 @@ def test_workspace_size_valid_problems(L):
 
 @pytest.mark.parametrize("field,value", [
     ("n1", 0), ("n1", 1000), ("alpha", 1.0), ("alpha", 2.0), ("alpha", float("nan")), ("dt", 0.0),
-    ("len1", -1.0), ("dim", 3), ("weights", 5), ("order", 3), ("scheme", 7),
+    ("len1", -1.0), ("dim", 3), ("weights", 5), ("order", 4), ("scheme", 7),
 ])
 def test_invalid_problem_rejected(L, field, value):
     o = fde.make_opts()
@@ -61,6 +61,14 @@ def test_invalid_problem_rejected(L, field, value):
     setattr(p, field, value)
     st, _ = _ws(p, o)
     assert st == fde.EINVAL
+
+
+def test_tridiagonal_preconditioner_is_1d_and_unshifted(L):
+    o = fde.make_opts()
+    assert _ws(fde.make_problem(1, 255, 1.5, 0.01, order="tri"), o)[0] == fde.OK
+    assert _ws(fde.make_problem(1, 255, 1.5, 0.01, order="tri", tau_shift=True), o)[0] == fde.EINVAL
+    p2 = fde.make_problem(2, 63, 1.3, 0.01, n2=63, beta=1.8, weights="wsgd2", order="tri")
+    assert _ws(p2, o)[0] == fde.EINVAL
 
 
 @pytest.mark.parametrize("field,value", [
