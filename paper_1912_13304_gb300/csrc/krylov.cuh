@@ -12,9 +12,13 @@
 // last phase is followed by the partial inner products <w, v_i> and ||w||^2
 // of the elements the CTA produced -- one reduction per iteration.
 // Classical Gram-Schmidt is reorthogonalised (a second pass) only when the
-// projection leaves less than a tenth of ||w|| (a Daniel-Gragg-Kaufman-
-// Stewart test), so the common step needs no second reduction.  For FP32
-// vectors the inner products use compensated FP32 arithmetic (team.cuh).
+// projection leaves less than ||w|| / sqrt(2) (the Daniel-Gragg-Kaufman-
+// Stewart test); the second pass updates w and forms its dots in one sweep.  For FP32
+// vectors the Gram-Schmidt inner products sum each thread's elements in FP32
+// (FMA) and the block and team partials in FP64; PCG's scalar products and the
+// right-hand side norms use compensated FP32 arithmetic (team.cuh).  A
+// compensated term costs about ten instructions, which made the basis passes
+// of the 2D inner solves instruction-bound.
 #pragma once
 
 #include <type_traits>
@@ -141,19 +145,24 @@ FDE_D bool dots_own(const Team& t, long long N, const W* a, const W* V, const do
             });
             block_sum<8>(acc, ks.red + c0, ks.wide);
         } else {
-            F2 acc[8];
+            // FP32 vectors of a Krylov basis: each thread sums its few elements in
+            // FP32 (FMA), the block and team sums run in FP64
+            float acc[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = F2{0.0f, 0.0f};
+            for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
             own([&](long long i) {
                 const float ai = (float)ldw(a + i);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int kk = c0 + k;
-                    if (kk < cnt) dot2_acc(acc[k], ai, (float)ldw(V + (long long)kk * N + i));
-                    else if (kk == cnt && norm) dot2_acc(acc[k], ai, ai);
+                    if (kk < cnt) acc[k] = fmaf(ai, (float)ldw(V + (long long)kk * N + i), acc[k]);
+                    else if (kk == cnt && norm) acc[k] = fmaf(ai, ai, acc[k]);
                 }
             });
-            block_sum_f2<8>(acc, ks.red + c0, ks.wide);
+            double part[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) part[k] = acc[k];
+            block_sum<8>(part, ks.red + c0, ks.wide);
         }
     }
     if (threadIdx.x < cnt) ks.red[threadIdx.x] *= vs[threadIdx.x];
@@ -193,9 +202,10 @@ FDE_D bool dots_basis(const Team& t, long long N, const W* a, const W* V, const 
             }
             block_sum<8>(acc, ks.red + c0, ks.wide);
         } else {
-            F2 acc[8];
+            // per-thread FP32 sums (FMA), FP64 block and team sums (see dots_own)
+            float acc[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = F2{0.0f, 0.0f};
+            for (int k = 0; k < 8; ++k) acc[k] = 0.0f;
             for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += 2 * nt) {
                 const long long i1 = i0 + nt;
                 const bool h1 = i1 < hi;
@@ -209,12 +219,12 @@ FDE_D bool dots_basis(const Team& t, long long N, const W* a, const W* V, const 
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
-                    if (c0 + k < tot) {
-                        dot2_acc(acc[k], a0, v0[k]);
-                        dot2_acc(acc[k], a1, v1[k]);
-                    }
+                    if (c0 + k < tot) acc[k] = fmaf(a1, v1[k], fmaf(a0, v0[k], acc[k]));
             }
-            block_sum_f2<8>(acc, ks.red + c0, ks.wide);
+            double part[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) part[k] = acc[k];
+            block_sum<8>(part, ks.red + c0, ks.wide);
         }
     }
     if (threadIdx.x < cnt) ks.red[threadIdx.x] *= vs[threadIdx.x];
@@ -269,13 +279,9 @@ template <typename W>
 FDE_NI bool reorth_fused(const Team& t, long long N, W* w, const W* V, const W* c, int cnt, KShared& ks) {
     long long lo, hi;
     team_range(t, N, lo, hi);
-    using Acc = typename std::conditional<sizeof(W) == 8, double, F2>::type;
-    Acc acc[kFusedMax + 1];
+    W acc[kFusedMax + 1];
 #pragma unroll
-    for (int q = 0; q <= kFusedMax; ++q) {
-        if constexpr (sizeof(W) == 8) acc[q] = 0.0;
-        else acc[q] = F2{0.0f, 0.0f};
-    }
+    for (int q = 0; q <= kFusedMax; ++q) acc[q] = W(0);
     for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         // every basis value of element i loaded once, into registers (static
         // indices under predicates), for both the update and the dots
@@ -288,35 +294,20 @@ FDE_NI bool reorth_fused(const Team& t, long long N, W* w, const W* V, const W* 
             if (k < cnt) a -= c[k] * v[k];
         w[i] = a;
 #pragma unroll
-        for (int k = 0; k < kFusedMax; ++k) {
-            if (k < cnt) {
-                if constexpr (sizeof(W) == 8) acc[k] += a * v[k];
-                else dot2_acc(acc[k], a, v[k]);
-            }
-        }
-        if constexpr (sizeof(W) == 8) acc[kFusedMax] += a * a;
-        else dot2_acc(acc[kFusedMax], a, a);
+        for (int k = 0; k < kFusedMax; ++k)
+            if (k < cnt) acc[k] += a * v[k];
+        acc[kFusedMax] += a * a;
     }
     // block sums of the cnt dots and the norm (entry cnt) in chunks of 8; the
     // loops below index acc only with compile-time constants
     for (int c0 = 0; c0 <= cnt; c0 += 8) {
-        if constexpr (sizeof(W) == 8) {
-            double part[8];
+        double part[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) part[k] = 0.0;
+        for (int k = 0; k < 8; ++k) part[k] = 0.0;
 #pragma unroll
-            for (int k = 0; k <= kFusedMax; ++k)
-                if (k >= c0 && k < c0 + 8 && k <= cnt) part[k - c0] = k == cnt ? acc[kFusedMax] : acc[k];
-            block_sum<8>(part, ks.red + c0, ks.wide);
-        } else {
-            F2 part[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) part[k] = F2{0.0f, 0.0f};
-#pragma unroll
-            for (int k = 0; k <= kFusedMax; ++k)
-                if (k >= c0 && k < c0 + 8 && k <= cnt) part[k - c0] = k == cnt ? acc[kFusedMax] : acc[k];
-            block_sum_f2<8>(part, ks.red + c0, ks.wide);
-        }
+        for (int k = 0; k <= kFusedMax; ++k)
+            if (k >= c0 && k < c0 + 8 && k <= cnt) part[k - c0] = (double)(k == cnt ? acc[kFusedMax] : acc[k]);
+        block_sum<8>(part, ks.red + c0, ks.wide);
     }
     if (threadIdx.x < cnt) ks.red[threadIdx.x] *= ks.vs[threadIdx.x];
     __syncthreads();
