@@ -401,13 +401,13 @@ FDE_NI bool arnoldi_right(const Team& t, const Inst& I, int lm, Combo<W> u, int 
     plane_dst_rows<W>(t, I, wk, u, nullptr, z);
     if (!team_sync(t)) return false;
     trace_mark(t, 21);
-    plane_tau_cols<W>(t, I, wk, z);
+    if (!plane_cols_tau<W>(t, I, wk, z)) return false;
     if (!team_sync(t)) return false;
     trace_mark(t, 22);
     plane_dst_matvec_rows<W>(t, I, wk, z, z, tmp);
     if (!team_sync(t)) return false;
     trace_mark(t, 11);
-    plane_matvec_cols<W>(t, I, wk, z, W(1), epi_mvy<W>(I, tmp, out_store<W>(w)));
+    if (!plane_cols_matvec<W>(t, I, wk, z, W(1), epi_mvy<W>(I, tmp, out_store<W>(w)))) return false;
     trace_mark(t, 13);
     // the column phase scatters each CTA's outputs over the plane: reduce over
     // contiguous ranges instead, once every CTA's part is written
