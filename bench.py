@@ -63,9 +63,9 @@ def parse():
                     help="side sections to time beside the headline (comma-separated; empty for none)")
     ap.add_argument("--only", default="", help="time only this section (headline or a side section) and print it")
     ap.add_argument("--side-steps", type=int, default=3, help="timed repetitions of each side section")
-    ap.add_argument("--inner-tol", type=float, default=1e-3,
+    ap.add_argument("--inner-tol", type=float, default=1e-4,
                     help="relative tolerance of each FP32 inner solve on the 4095^2 planes (the march and the "
-                         "Crank-Nicolson step); 1e-3 measured fastest there (1e-3 .. 1e-6 swept)")
+                         "Crank-Nicolson step)")
     return ap.parse_args()
 
 

@@ -13,15 +13,13 @@
 // of the elements the CTA produced -- one reduction per iteration.
 // Classical Gram-Schmidt is reorthogonalised (a second pass) only when the
 // projection leaves less than ||w|| / sqrt(2) (the Daniel-Gragg-Kaufman-
-// Stewart test); the second pass updates w and forms its dots in one sweep.  For FP32
+// Stewart test).  For FP32
 // vectors the Gram-Schmidt inner products sum each thread's elements in FP32
 // (FMA) and the block and team partials in FP64; PCG's scalar products and the
 // right-hand side norms use compensated FP32 arithmetic (team.cuh).  A
 // compensated term costs about ten instructions, which made the basis passes
 // of the 2D inner solves instruction-bound.
 #pragma once
-
-#include <type_traits>
 
 #include "ops.cuh"
 
@@ -265,53 +263,6 @@ FDE_D void form_basis(const Team& t, long long N, const W* w, const W* V, const 
         out[i0] = a0;
         if (h1) out[i1] = a1;
     }
-}
-
-// The second classical Gram-Schmidt pass in one sweep over this CTA's part of
-// the team range: w <- w - sum_{q < cnt} c_q V_q, and, from the same loads
-// held in registers, ks.red[q] = <w, vs_q V_q> (q < cnt) and ks.red[cnt] =
-// <w, w> of the updated w, then summed over the team.  Two separate passes
-// read the basis twice.  For cnt <= kFusedMax; the basis values and the
-// accumulators stay in registers.
-constexpr int kFusedMax = 20;
-
-template <typename W>
-FDE_NI bool reorth_fused(const Team& t, long long N, W* w, const W* V, const W* c, int cnt, KShared& ks) {
-    long long lo, hi;
-    team_range(t, N, lo, hi);
-    W acc[kFusedMax + 1];
-#pragma unroll
-    for (int q = 0; q <= kFusedMax; ++q) acc[q] = W(0);
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        // every basis value of element i loaded once, into registers (static
-        // indices under predicates), for both the update and the dots
-        W v[kFusedMax];
-#pragma unroll
-        for (int k = 0; k < kFusedMax; ++k) v[k] = k < cnt ? ldw(V + (long long)k * N + i) : W(0);
-        W a = ldw(w + i);
-#pragma unroll
-        for (int k = 0; k < kFusedMax; ++k)
-            if (k < cnt) a -= c[k] * v[k];
-        w[i] = a;
-#pragma unroll
-        for (int k = 0; k < kFusedMax; ++k)
-            if (k < cnt) acc[k] += a * v[k];
-        acc[kFusedMax] += a * a;
-    }
-    // block sums of the cnt dots and the norm (entry cnt) in chunks of 8; the
-    // loops below index acc only with compile-time constants
-    for (int c0 = 0; c0 <= cnt; c0 += 8) {
-        double part[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) part[k] = 0.0;
-#pragma unroll
-        for (int k = 0; k <= kFusedMax; ++k)
-            if (k >= c0 && k < c0 + 8 && k <= cnt) part[k - c0] = (double)(k == cnt ? acc[kFusedMax] : acc[k]);
-        block_sum<8>(part, ks.red + c0, ks.wide);
-    }
-    if (threadIdx.x < cnt) ks.red[threadIdx.x] *= ks.vs[threadIdx.x];
-    __syncthreads();
-    return team_allreduce(t, ks.red, cnt + 1);
 }
 
 // ks.red[k] = <a_k, b_k> for up to 8 pairs over the team partition.
@@ -567,15 +518,10 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
                     ks.y[threadIdx.x] = ks.red[threadIdx.x];
                 }
                 __syncthreads();
-                if (j + 1 <= kFusedMax) {
-                    trace_mark(t, 32);
-                    if (!reorth_fused<W>(t, N, v.w, v.V, kcoef<W>(ks), j + 1, ks)) return false;
-                } else {
-                    form_basis<W>(t, N, v.w, v.V, kcoef<W>(ks), j + 1, v.w);
-                    __syncthreads();
-                    trace_mark(t, 32);
-                    if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
-                }
+                form_basis<W>(t, N, v.w, v.V, kcoef<W>(ks), j + 1, v.w);
+                __syncthreads();
+                trace_mark(t, 32);
+                if (!dots_basis<W>(t, N, v.w, v.V, ks.vs, j + 1, true, ks)) return false;
                 trace_mark(t, 31);
                 if (threadIdx.x == 0) ks.sc[1] = ks.red[j + 1] - sum_squares(ks.red, j + 1);
                 if (threadIdx.x <= j) {
