@@ -761,10 +761,12 @@ FDE_HD int col4_group(const Inst& I, int bytes, int sets) {
     return G;
 }
 
-// Stage A: the extension of column c (get(c, k, direct) returns r_k of column
-// c, 1 <= k <= n2, for c < n1) packed, P1-point FFTs, twiddled, into Y.
-template <typename W, int EXT, typename GetF>
-FDE_NI void col4_fwd(const Team& t, const Inst& I, const Wk& wk, int G, cx<W>* Y, GetF get) {
+// Stage A: the extension of column c of s * src (pitch n1; r_k at row k - 1)
+// packed, P1-point FFTs, twiddled, into Y.  Every operand is an argument (no
+// captured references): a non-inlined function reaches a captured local only
+// through memory, on every element.
+template <typename W, int EXT>
+FDE_NI void col4_fwd(const Team& t, const Inst& I, const Wk& wk, int G, cx<W>* Y, const W* src, W s) {
     const Col4 g = col4_geom(I);
     cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const cx<W>* gt = tw_global_table<W>(wk.tw);
@@ -773,20 +775,18 @@ FDE_NI void col4_fwd(const Team& t, const Inst& I, const Wk& wk, int G, cx<W>* Y
     const int units = g.tiles * groups;
     const int nt = blockDim.x;
     const int c = threadIdx.x & (kColTile - 1);
+    const int total = G * g.P1 * kColTile;
     for (int un = t.rank; un < units; un += t.size) {
         const int tile = un / groups, m2b = (un - tile * groups) * G;
         const int col = tile * kColTile + c;
-        // (m1, g) of this thread's elements: idx = (g P1 + m1) kColTile + c
-        const int total = G * g.P1 * kColTile;
+        const W* base = src + col;
+        auto get = [&](int k, bool) { return s * ldw(base + (long long)(k - 1) * g.n1); };
         for (int idx = threadIdx.x; idx < total; idx += nt) {
             const int r = idx >> 5;                 // kColTile == 32
             const int m1 = r & (g.P1 - 1), gg = r >> g.logP1;
             const int m = g.P2 * m1 + m2b + gg;
             cx<W> v = mk(W(0), W(0));
-            if (col < g.n1) {
-                auto gc = [&](int k, bool d) { return get(col, k, d); };
-                v = pack_elem<W, EXT>(gc, m, g.n2, g.Np);
-            }
+            if (col < g.n1) v = pack_elem<W, EXT>(get, m, g.n2, g.Np);
             buf[pad((gg * kColTile + c) * g.ls1 + m1)] = v;
         }
         __syncthreads();
@@ -806,7 +806,7 @@ FDE_NI void col4_fwd(const Team& t, const Inst& I, const Wk& wk, int G, cx<W>* Y
 // mu (col_base + c is kMulTau2's x-frequency), inverse FFTs, inverse twiddle;
 // in place in Y (and the second output set in Y2 for kMulLam2).
 template <typename W>
-FDE_NI void col4_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>& mu, cx<W>* Y, cx<W>* Y2) {
+FDE_NI void col4_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W> mu, cx<W>* Y, cx<W>* Y2) {
     const Col4 g = col4_geom(I);
     cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const cx<W>* gt = tw_global_table<W>(wk.tw);
@@ -822,6 +822,7 @@ FDE_NI void col4_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>&
         const int tile = un / runits, u = un - tile * runits;
         int rows[2], nrows;
         split_row_unit(u, g.P1, rows, nrows);
+        const int row0 = rows[0], row1 = rows[1];
         const long long cb = (long long)tile * kColTile + c;
         // line (slot, c) holds row rows[slot]; element m2
         const int total = 2 * g.P2 * kColTile;
@@ -829,7 +830,7 @@ FDE_NI void col4_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>&
             const int r = idx >> 5;
             const int m2 = r & (g.P2 - 1), slot = r >> g.logP2;
             cx<W> v = mk(W(0), W(0));
-            if (slot < nrows) v = ldw(Y + ((long long)rows[slot] * g.P2 + m2) * g.n1p + cb);
+            if (slot < nrows) v = ldw(Y + ((long long)(slot ? row1 : row0) * g.P2 + m2) * g.n1p + cb);
             buf[pad((slot * kColTile + c) * g.ls2 + m2)] = v;
         }
         __syncthreads();
@@ -841,7 +842,7 @@ FDE_NI void col4_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>&
         for (int idx = threadIdx.x; idx < npairs * kColTile; idx += nt) {
             const int j2 = idx >> 5;
             const int j2m = u == 0 ? ((g.P2 - j2) & (g.P2 - 1)) : g.P2 - 1 - j2;
-            const int j = rows[0] + g.P1 * j2;
+            const int j = row0 + g.P1 * j2;
             const cx<W> wj = tw_L<W>(wk.tw, j, g.logNp + 1);
             const int ia = c * g.ls2 + j2, ib = (sm * kColTile + c) * g.ls2 + j2m;
             cx<W> a, bb, al, be, al2, be2;
@@ -866,7 +867,7 @@ FDE_NI void col4_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>&
             const int r = idx >> 5;
             const int m2 = r & (g.P2 - 1), slot = r >> g.logP2;
             if (slot >= nrows) continue;
-            const int j1 = rows[slot];
+            const int j1 = slot ? row1 : row0;
             const cx<W> w = conj(gt[(j1 * m2) << tsh]);
             const long long at = ((long long)j1 * g.P2 + m2) * g.n1p + cb;
             const int li = (slot * kColTile + c) * g.ls2 + m2;
@@ -878,11 +879,12 @@ FDE_NI void col4_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>&
 }
 
 // Stage C: inverse P1-point FFTs of each m2 group's lines (both sets when two)
-// and the real outputs a_k (b_k) of rows k - 1 = 2m + e - 1 handed to
-// put(row, col, a, b, fetch(row, col)); fetches run ahead of their puts.
-template <typename W, bool TWO, typename FetchF, typename PutF>
-FDE_NI void col4_inv(const Team& t, const Inst& I, const Wk& wk, int G, const cx<W>* Y, const cx<W>* Y2,
-                    FetchF fetch, PutF put) {
+// and the real outputs a_k (b_k) of rows k - 1 = 2m + e - 1: stored to out
+// (pitch n1) when EPI is false, else through epi (its operands fetched for
+// kUnpackUnroll elements before any of them is stored).
+template <typename W, bool TWO, bool EPI>
+FDE_NI void col4_inv(const Team& t, const Inst& I, const Wk& wk, int G, const cx<W>* Y, const cx<W>* Y2, W* out,
+                     const Epi<W> epi) {
     const Col4 g = col4_geom(I);
     cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const int groups = g.P2 / G;
@@ -891,10 +893,11 @@ FDE_NI void col4_inv(const Team& t, const Inst& I, const Wk& wk, int G, const cx
     const int c = threadIdx.x & (kColTile - 1);
     const int nl = G * kColTile;
     const int o2 = nl * g.ls1;
+    const int total = G * g.P1 * kColTile;
+    const int outs = G * (g.P1 / 2) * 2 * kColTile;
     for (int un = t.rank; un < units; un += t.size) {
         const int tile = un / groups, m2b = (un - tile * groups) * G;
         const int col = tile * kColTile + c;
-        const int total = G * g.P1 * kColTile;
         for (int idx = threadIdx.x; idx < total; idx += nt) {
             const int r = idx >> 5;
             const int j1 = r & (g.P1 - 1), gg = r >> g.logP1;
@@ -907,16 +910,14 @@ FDE_NI void col4_inv(const Team& t, const Inst& I, const Wk& wk, int G, const cx
         fft_lines<W, true>(buf, g.logP1, TWO ? 2 * nl : nl, g.ls1, wk.tw);
         // outputs: element m1 < P1/2 of line (gg, c) carries rows 2m - 1 and 2m
         // (k = 2m, 2m + 1), m = P2 m1 + m2
-        const int outs = G * (g.P1 / 2) * 2 * kColTile;
-        using Ops = decltype(fetch(0, 0));
         constexpr int U = kUnpackUnroll;
         for (int base = threadIdx.x; base < outs; base += U * nt) {
-            Ops ops[U];
+            typename Epi<W>::Ops ops[U];
             W va[U], vb[U];
-            int rowi[U];
+            long long at[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                rowi[u] = -1;
+                at[u] = -1;
                 const int idx = base + u * nt;
                 if (idx < outs && col < g.n1) {
                     const int r = idx >> 5;
@@ -924,8 +925,8 @@ FDE_NI void col4_inv(const Team& t, const Inst& I, const Wk& wk, int G, const cx
                     const int m1 = q & (g.P1 / 2 - 1), gg = q >> (g.logP1 - 1);
                     const int k = 2 * (g.P2 * m1 + m2b + gg) + e;
                     if (k >= 1 && k <= g.n2) {
-                        rowi[u] = k - 1;
-                        ops[u] = fetch(k - 1, col);
+                        at[u] = (long long)(k - 1) * g.n1 + col;
+                        if (EPI) ops[u] = epi.fetch(at[u]);
                         const int li = (gg * kColTile + c) * g.ls1 + m1;
                         const cx<W> z = buf[pad(li)];
                         va[u] = e ? z.y : z.x;
@@ -938,8 +939,11 @@ FDE_NI void col4_inv(const Team& t, const Inst& I, const Wk& wk, int G, const cx
                 }
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (rowi[u] >= 0) put(rowi[u], col, va[u], vb[u], ops[u]);
+            for (int u = 0; u < U; ++u) {
+                if (at[u] < 0) continue;
+                if (EPI) epi.put(at[u], va[u], vb[u], ops[u]);
+                else out[at[u]] = va[u];
+            }
         }
         __syncthreads();
     }
@@ -949,16 +953,12 @@ FDE_NI void col4_inv(const Team& t, const Inst& I, const Wk& wk, int G, const cx
 // three stages; false if a barrier timed out.
 template <typename W>
 FDE_NI bool col4_tau(const Team& t, const Inst& I, const Wk& wk, W* z, int G) {
-    const Col4 g = col4_geom(I);
     cx<W>* Y = reinterpret_cast<cx<W>*>(I.col4);
-    col4_fwd<W, kExtOdd>(t, I, wk, G, Y, [&](int col, int k, bool) {
-        return ldw(z + (long long)(k - 1) * g.n1 + col);
-    });
+    col4_fwd<W, kExtOdd>(t, I, wk, G, Y, z, W(1));
     if (!team_sync(t)) return false;
     col4_rows<W>(t, I, wk, mult_tau2<W>(I), Y, nullptr);
     if (!team_sync(t)) return false;
-    col4_inv<W, false>(t, I, wk, G, Y, nullptr, [](int, int) { return NoOps{}; },
-                       [&](int row, int col, W va, W, const NoOps&) { z[(long long)row * g.n1 + col] = va; });
+    col4_inv<W, false, false>(t, I, wk, G, Y, nullptr, z, Epi<W>{});
     return true;
 }
 
@@ -967,21 +967,14 @@ FDE_NI bool col4_tau(const Team& t, const Inst& I, const Wk& wk, W* z, int G) {
 template <typename W>
 FDE_NI bool col4_matvec(const Team& t, const Inst& I, const Wk& wk, const W* x, W s, Epi<W> epi, int G) {
     const Col4 g = col4_geom(I);
-    const bool sym = I.symy;
     cx<W>* Y = reinterpret_cast<cx<W>*>(I.col4);
     cx<W>* Y2 = Y + (long long)g.Np * g.n1p;
-    col4_fwd<W, kExtZero>(t, I, wk, G, Y, [&](int col, int k, bool) {
-        return s * ldw(x + (long long)(k - 1) * g.n1 + col);
-    });
+    col4_fwd<W, kExtZero>(t, I, wk, G, Y, x, s);
     if (!team_sync(t)) return false;
-    col4_rows<W>(t, I, wk, mult_matvec<W>(I.ax[1], sym), Y, Y2);
+    col4_rows<W>(t, I, wk, mult_matvec<W>(I.ax[1], I.symy), Y, Y2);
     if (!team_sync(t)) return false;
-    auto fe = [&](int row, int col) { return epi.fetch((long long)row * g.n1 + col); };
-    auto pu = [&](int row, int col, W va, W vb, const typename Epi<W>::Ops& r) {
-        epi.put((long long)row * g.n1 + col, va, vb, r);
-    };
-    if (sym) col4_inv<W, false>(t, I, wk, G, Y, Y2, fe, pu);
-    else col4_inv<W, true>(t, I, wk, G, Y, Y2, fe, pu);
+    if (I.symy) col4_inv<W, false, true>(t, I, wk, G, Y, Y2, nullptr, epi);
+    else col4_inv<W, true, true>(t, I, wk, G, Y, Y2, nullptr, epi);
     return true;
 }
 
