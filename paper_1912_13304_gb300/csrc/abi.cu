@@ -142,7 +142,7 @@ struct Layout {
     size_t inst, sync, tw64, tw32;
     size_t lam64[2], lam32[2], phi64[2], phi32[2];
     size_t dinv64, dinv32, dp32, dm32, ep32, em32;
-    size_t r64, t64, wvec, split64, split32, wts, dbar, tri64, tri32, trisc, col4;
+    size_t r64, t64, wvec, split64, split32, wts, dbar, tri64, tri32, trisc;
     size_t total;
     int TW, logTW;
     int Np[2];
@@ -198,12 +198,6 @@ Layout layout(const fde_problem* p, const fde_solve_opts* o) {
     L.split32 = take((size_t)2 * npmax * sizeof(cx<float>));
     L.wts = take((size_t)(npmax + 2) * sizeof(double));
     L.dbar = take(sizeof(double));
-    if (p->dim == 2 && ilog2(L.Np[1]) >= 8) {
-        // the y lines' four-step intermediates: two sets of Np2 x (n1 padded to
-        // whole column tiles) complex values, sized for FP64
-        const size_t n1p = (size_t)((p->n1 + kColTile - 1) / kColTile) * kColTile;
-        L.col4 = take((size_t)2 * L.Np[1] * n1p * sizeof(cx<double>));
-    }
     if (p->order == FDE_ORDER_TRI) {
         L.tri64 = take((size_t)3 * N * sizeof(double));
         L.tri32 = take((size_t)3 * N * sizeof(float));
@@ -641,7 +635,6 @@ fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* op
     I.tri64 = tri ? at<double>(workspace, Lo.tri64) : nullptr;
     I.tri32 = tri ? at<float>(workspace, Lo.tri32) : nullptr;
     I.trisc = tri ? at<void>(workspace, Lo.trisc) : nullptr;
-    I.col4 = Lo.col4 ? at<void>(workspace, Lo.col4) : nullptr;
     I.wvec = at<void>(workspace, Lo.wvec);
     I.r64 = at<double>(workspace, Lo.r64);
     I.t64 = at<double>(workspace, Lo.t64);

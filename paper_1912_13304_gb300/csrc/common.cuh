@@ -82,7 +82,6 @@ struct Inst {
     const double* tri64;               // P_tri: [3N] lower, diagonal, upper of M (else null)
     const float* tri32;
     void* trisc;                       // P_tri on split lines: 8N elements of cyclic-reduction state
-    void* col4;                        // 2D: the y-axis four-step intermediates Y, Y2 (else null)
     // solver workspace
     void* wvec;                        // vectors of the working precision
     double* r64;                       // FP64 outer residual (refinement modes)

@@ -266,66 +266,69 @@ FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, 
 // slower overall.
 template <typename R> constexpr int kFftItems = 1;
 
-// Radix schedule of a 2^logP-point FFT: log2 of each pass's radix, written to
-// lr[] (at most 8 passes); returns the number of passes.  FP64 takes radix-8
-// passes and one radix-4 or radix-2 remainder.  FP32 takes radix-16 passes
-// (twice the work between two CTA barriers, and the registers to hold it)
-// and makes the smallest radix as large as possible, since the widest pass
-// bounds the lines one call can take.
-FDE_HD int fft_schedule(int logP, int elem_bytes, int* lr) {
+// Radix schedule of a 2^logP-point FFT, packed: log2 of pass i's radix in
+// bits [4i, 4i + 4), zero after the last pass (at most 8 passes).  A packed
+// word stays in a register, where an array indexed by the pass number would
+// live in local memory and cost a load at the start of every pass.  FP64
+// takes radix-8 passes and one radix-4 or radix-2 remainder.  FP32 takes
+// radix-16 passes (twice the work between two CTA barriers, and the
+// registers to hold it) and makes the smallest radix as large as possible,
+// since the widest pass bounds the lines one call can take.
+FDE_HD unsigned fft_schedule(int logP, int elem_bytes) {
+    unsigned s = 0;
     int n = 0;
+    auto put = [&](int lr) { s |= (unsigned)lr << (4 * n++); };
     if (elem_bytes == 8) {
         int rem = logP;
-        while (rem >= 3) { lr[n++] = 3; rem -= 3; }
-        if (rem > 0) lr[n++] = rem;
-        return n;
+        while (rem >= 3) { put(3); rem -= 3; }
+        if (rem > 0) put(rem);
+        return s;
     }
     const int n16 = logP / 4, r = logP % 4;
     int k16 = n16;
     if (r == 2 && n16 >= 1) k16 = n16 - 1;
     if (r == 1) k16 = n16 >= 2 ? n16 - 2 : 0;
-    for (int i = 0; i < k16; ++i) lr[n++] = 4;
-    if (r == 3) lr[n++] = 3;
+    for (int i = 0; i < k16; ++i) put(4);
+    if (r == 3) put(3);
     else if (r == 2) {
-        if (n16 >= 1) { lr[n++] = 3; lr[n++] = 3; } else lr[n++] = 2;
+        if (n16 >= 1) { put(3); put(3); } else put(2);
     } else if (r == 1) {
-        if (n16 >= 2) { lr[n++] = 3; lr[n++] = 3; lr[n++] = 3; }
-        else if (n16 == 1) { lr[n++] = 3; lr[n++] = 2; }
-        else lr[n++] = 1;
+        if (n16 >= 2) { put(3); put(3); put(3); }
+        else if (n16 == 1) { put(3); put(2); }
+        else put(1);
     }
-    return n;
+    return s;
 }
 
 template <typename R, bool INV>
 FDE_D void fft_inplace(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
     constexpr int K = kFftItems<R>;
     const bool smem_tw = logP <= tw.logT;
-    int lr[8];
-    const int np = fft_schedule(logP, (int)sizeof(R), lr);
     int logNs = 0;
-    for (int i = 0; i < np; ++i) {
+    for (unsigned s = fft_schedule(logP, (int)sizeof(R)); s != 0; s >>= 4) {
+        const int lr = (int)(s & 15u);
         if constexpr (sizeof(R) == 4) {
-            if (lr[i] == 4) {
+            if (lr == 4) {
                 stockham_pass_inplace<R, 16, 16 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
                 logNs += 4;
                 continue;
             }
         }
-        if (lr[i] == 3) stockham_pass_inplace<R, 8, 8 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
-        else if (lr[i] == 2) stockham_pass_inplace<R, 4, 4 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        if (lr == 3) stockham_pass_inplace<R, 8, 8 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        else if (lr == 2) stockham_pass_inplace<R, 4, 4 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
         else stockham_pass_inplace<R, 2, 2 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
-        logNs += lr[i];
+        logNs += lr;
     }
 }
 
 // Radix items per line of the widest pass (the one with the smallest radix),
 // and the lines one call of fft_inplace can take.
 FDE_HD int fft_items_per_line(int logP, int elem_bytes) {
-    int lr[8];
-    const int np = fft_schedule(logP, elem_bytes, lr);
+    const unsigned s0 = fft_schedule(logP, elem_bytes);
+    if (s0 == 0) return 1;
     int mn = 4;
-    for (int i = 0; i < np; ++i) mn = lr[i] < mn ? lr[i] : mn;
-    return np > 0 ? 1 << (logP - mn) : 1;
+    for (unsigned s = s0; s != 0; s >>= 4) mn = (int)(s & 15u) < mn ? (int)(s & 15u) : mn;
+    return 1 << (logP - mn);
 }
 FDE_HD int fft_lines_per_call(int logP, int threads, int elem_bytes) {
     return threads * (elem_bytes == 4 ? kFftItems<float> : kFftItems<double>) / fft_items_per_line(logP, elem_bytes);
@@ -336,11 +339,8 @@ FDE_HD int fft_lines_per_call(int logP, int threads, int elem_bytes) {
 // lstride), which commutes with pad() because lstride is a multiple of 16
 // whenever more than one batch is needed.  A single line with more radix
 // items than kFftItems<R> per thread is not supported (callers split such
-// lines).
-//
-// Not inlined: the radix passes then get the whole register budget of the
-// thread instead of what the calling phase leaves (its live state is saved
-// once per call, not held across every pass).
+// lines).  Not inlined: the radix passes then get the whole register budget
+// of the thread instead of what a calling phase with much live state leaves.
 template <typename R, bool INV>
 FDE_NI void fft_lines(cx<R>* buf, int logP, int nlines, int lstride, const Tw tw) {
     const int cap = fft_lines_per_call(logP, blockDim.x, (int)sizeof(R));

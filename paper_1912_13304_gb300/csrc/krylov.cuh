@@ -120,10 +120,6 @@ FDE_D double sum_squares(const double* v, int n) {
 // Reductions over N-vectors
 // ---------------------------------------------------------------------------
 
-// Basis vectors one sweep of dots_basis or form_basis takes: accumulators or
-// loads in registers.
-template <typename W> constexpr int kDotsOnePass = sizeof(W) == 4 ? 24 : 12;
-
 // ks.red[i] = <a, vs_i V_i> for i < cnt; with `norm`, ks.red[cnt] = <a, a>,
 // summed over the elements that own(f) visits (f(p) per element, threads of
 // this CTA), then over the team.
@@ -173,53 +169,15 @@ FDE_D bool dots_own(const Team& t, long long N, const W* a, const W* V, const do
     return team_allreduce(t, ks.red, tot);
 }
 
-// The same over the team's contiguous ranges: up to kDotsOnePass vectors in
-// one sweep, else chunks of 8 with each thread keeping two elements' loads of
-// 8 vectors in flight.
+// The same over the team's contiguous ranges: each thread keeps two elements'
+// loads of 8 vectors in flight.
 template <typename W>
-FDE_NI bool dots_basis(const Team& t, long long N, const W* a, const W* V, const double* vs, int cnt, bool norm,
-                       KShared& ks) {
+FDE_D bool dots_basis(const Team& t, long long N, const W* a, const W* V, const double* vs, int cnt, bool norm,
+                      KShared& ks) {
     long long lo, hi;
     team_range(t, N, lo, hi);
     const int tot = cnt + (norm ? 1 : 0);
     const int nt = blockDim.x;
-    constexpr int K1 = kDotsOnePass<W>;
-    if (tot <= K1) {
-        // one sweep: every vector's accumulator in a register (compile-time
-        // indices under predicates), the loads of two elements of every vector
-        // in flight together, and `a` read once instead of once per 8 vectors
-        W acc[K1];
-#pragma unroll
-        for (int k = 0; k < K1; ++k) acc[k] = W(0);
-        for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += 2 * nt) {
-            const long long i1 = i0 + nt;
-            const bool h1 = i1 < hi;
-            const W a0 = ldw(a + i0), a1 = h1 ? ldw(a + i1) : W(0);
-#pragma unroll
-            for (int k = 0; k < K1; ++k) {
-                if (k < cnt) {
-                    const W v0 = ldw(V + (long long)k * N + i0);
-                    const W v1 = h1 ? ldw(V + (long long)k * N + i1) : W(0);
-                    acc[k] += a0 * v0 + a1 * v1;
-                } else if (k == cnt && norm) {
-                    acc[k] += a0 * a0 + a1 * a1;
-                }
-            }
-        }
-        for (int c0 = 0; c0 < tot; c0 += 8) {
-            double part[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) part[k] = 0.0;
-#pragma unroll
-            for (int k = 0; k < K1; ++k)
-                if (k >= c0 && k < c0 + 8) part[k - c0] = (double)acc[k];
-            block_sum<8>(part, ks.red + c0, ks.wide);
-        }
-        if (threadIdx.x < cnt) ks.red[threadIdx.x] *= vs[threadIdx.x];
-        __syncthreads();
-        trace_mark(t, 60);
-        return team_allreduce(t, ks.red, tot);
-    }
     for (int c0 = 0; c0 < tot; c0 += 8) {
         if constexpr (sizeof(W) == 8) {
             double acc[8];
@@ -276,32 +234,10 @@ FDE_NI bool dots_basis(const Team& t, long long N, const W* a, const W* V, const
 // V_j = w - sum_{q < cnt} c_q V_q over this CTA's contiguous part of the team
 // range, two elements and four vectors of loads in flight per thread.
 template <typename W>
-FDE_NI void form_basis(const Team& t, long long N, const W* w, const W* V, const W* c, int cnt, W* out) {
+FDE_D void form_basis(const Team& t, long long N, const W* w, const W* V, const W* c, int cnt, W* out) {
     long long lo, hi;
     team_range(t, N, lo, hi);
     const int nt = blockDim.x;
-    constexpr int K1 = kDotsOnePass<W>;
-    if (cnt <= K1) {
-        // every vector's loads of the two elements issued together (compile-time
-        // indices under predicates); the same order of subtraction as below
-        for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += 2 * nt) {
-            const long long i1 = i0 + nt;
-            const bool h1 = i1 < hi;
-            W a0 = ldw(w + i0), a1 = h1 ? ldw(w + i1) : W(0);
-#pragma unroll
-            for (int k = 0; k < K1; ++k) {
-                if (k < cnt) {
-                    const W v0 = ldw(V + (long long)k * N + i0);
-                    const W v1 = h1 ? ldw(V + (long long)k * N + i1) : W(0);
-                    a0 -= c[k] * v0;
-                    a1 -= c[k] * v1;
-                }
-            }
-            out[i0] = a0;
-            if (h1) out[i1] = a1;
-        }
-        return;
-    }
     for (long long i0 = lo + threadIdx.x; i0 < hi; i0 += 2 * nt) {
         const long long i1 = i0 + nt;
         const bool h1 = i1 < hi;
@@ -558,9 +494,19 @@ FDE_NI bool gmres_right_core(const Team& t, const Inst& I, int lm, const W* rhs,
             if (threadIdx.x == 0) {
                 const double ww = ks.red[j + 1];
                 const double hh = sum_squares(ks.red, j + 1);
-                // ||w - V h|| > ||w|| / sqrt(2) (the Daniel-Gragg-Kaufman-Stewart
-                // criterion): one classical Gram-Schmidt pass is enough
-                const bool once = hh < 0.5 * ww;
+                // ||w - V h|| > eta ||w|| (the Daniel-Gragg-Kaufman-Stewart test):
+                // one classical Gram-Schmidt pass is enough.  eta = 1/sqrt(2),
+                // except in an FP32 inner solve asked for a loose tolerance: one
+                // pass leaves the new vector's orthogonality to the basis at about
+                // u ||w|| / ||w - V h||, and while that stays a hundredth of the
+                // inner tolerance a second pass buys nothing the outer FP64
+                // refinement would see.
+                double eta2 = 0.5;
+                if (sizeof(W) == 4 && sp.inner) {
+                    const double e = 5.96e-8 / (0.01 * sp.tol);
+                    eta2 = e * e < 0.5 ? e * e : 0.5;
+                }
+                const bool once = ww - hh > eta2 * ww;
                 ks.sc[0] = once ? 0.0 : 1.0;
                 ks.sc[1] = ww - hh;
                 if (once) {

@@ -705,279 +705,6 @@ FDE_NI void plane_tau_cols(const Team& t, const Inst& I, const Wk& wk, W* z) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// 2D plane, y lines as a four-step FFT over the whole plane.  A y line of
-// Np = n2 + 1 packed points is split Np = P1 x P2 (m = P2 m1 + m2, j = j1 +
-// P1 j2) as in the 1D split layout, and the plane's n1 lines move together in
-// tiles of kColTile adjacent columns, so every global access is a row segment
-// of kColTile elements (128 or 256 bytes) instead of the few columns a CTA
-// could hold whole lines of:
-//   A: per (tile, group of m2): pack, P1-point FFTs over m1, twiddle
-//      W_Np^(j1 m2) -> Y[j1][m2][c];
-//   B: per (tile, rows {j1, P1 - j1}): P2-point FFTs over m2, the spectral
-//      step on the pairs (j, Np - j), inverse FFTs, inverse twiddle -> Y, Y2;
-//   C: per (tile, group of m2): inverse P1-point FFTs over j1, unpack, epilogue.
-// Y and Y2 live in the plan's workspace (I.col4), c fastest with the columns
-// padded to whole tiles (n1p).  A team barrier separates the stages.
-// ---------------------------------------------------------------------------
-
-constexpr int kColTile = 32;
-static_assert(kColTile == 32, "the column stages map lanes to the columns of a tile (idx >> 5)");
-
-struct Col4 {
-    int n1, n2, Np, logNp, P1, P2, logP1, logP2, n1p, tiles, ls1, ls2;
-};
-
-FDE_HD Col4 col4_geom(const Inst& I) {
-    Col4 g;
-    const AxisData& A = I.ax[1];
-    g.n1 = I.n1;
-    g.n2 = A.n;
-    g.Np = A.Np;
-    g.logNp = A.logNp;
-    g.logP1 = A.logNp / 2;
-    g.logP2 = A.logNp - g.logP1;
-    g.P1 = 1 << g.logP1;
-    g.P2 = 1 << g.logP2;
-    g.tiles = (I.n1 + kColTile - 1) / kColTile;
-    g.n1p = g.tiles * kColTile;
-    g.ls1 = g.P1 + 16;          // line strides: a multiple of 16, and consecutive
-    g.ls2 = g.P2 + 16;          // lines of a tile fall on different banks
-    return g;
-}
-
-// Lines of a stage that fit the work area: stage B needs 2 kColTile lines per
-// output set; stages A and C take as many m2 values per unit (a power of two)
-// as fit.  0 when the four-step layout does not apply (short lines, or no
-// scratch).
-template <typename W>
-FDE_HD int col4_group(const Inst& I, int bytes, int sets) {
-    if (I.dim != 2 || !I.col4 || I.ax[1].logNp < 8) return 0;
-    const Col4 g = col4_geom(I);
-    const long long esz = sizeof(cx<W>);
-    if ((long long)padded_len(2 * sets * kColTile * g.ls2) * esz > bytes - 64) return 0;
-    int G = g.P2;
-    while (G > 0 && (long long)padded_len(sets * G * kColTile * g.ls1) * esz > bytes - 64) G >>= 1;
-    return G;
-}
-
-// Stage A: the extension of column c of s * src (pitch n1; r_k at row k - 1)
-// packed, P1-point FFTs, twiddled, into Y.  Every operand is an argument (no
-// captured references): a non-inlined function reaches a captured local only
-// through memory, on every element.
-template <typename W, int EXT>
-FDE_NI void col4_fwd(const Team& t, const Inst& I, const Wk& wk, int G, cx<W>* Y, const W* src, W s) {
-    const Col4 g = col4_geom(I);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
-    const cx<W>* gt = tw_global_table<W>(wk.tw);
-    const int tsh = wk.tw.logTW - g.logNp;
-    const int groups = g.P2 / G;
-    const int units = g.tiles * groups;
-    const int nt = blockDim.x;
-    const int c = threadIdx.x & (kColTile - 1);
-    const int total = G * g.P1 * kColTile;
-    for (int un = t.rank; un < units; un += t.size) {
-        const int tile = un / groups, m2b = (un - tile * groups) * G;
-        const int col = tile * kColTile + c;
-        const W* base = src + col;
-        auto get = [&](int k, bool) { return s * ldw(base + (long long)(k - 1) * g.n1); };
-        for (int idx = threadIdx.x; idx < total; idx += nt) {
-            const int r = idx >> 5;                 // kColTile == 32
-            const int m1 = r & (g.P1 - 1), gg = r >> g.logP1;
-            const int m = g.P2 * m1 + m2b + gg;
-            cx<W> v = mk(W(0), W(0));
-            if (col < g.n1) v = pack_elem<W, EXT>(get, m, g.n2, g.Np);
-            buf[pad((gg * kColTile + c) * g.ls1 + m1)] = v;
-        }
-        __syncthreads();
-        fft_lines<W, false>(buf, g.logP1, G * kColTile, g.ls1, wk.tw);
-        for (int idx = threadIdx.x; idx < total; idx += nt) {
-            const int r = idx >> 5;
-            const int j1 = r & (g.P1 - 1), gg = r >> g.logP1;
-            const int m2 = m2b + gg;
-            Y[((long long)j1 * g.P2 + m2) * g.n1p + tile * kColTile + c] =
-                buf[pad((gg * kColTile + c) * g.ls1 + j1)] * gt[(j1 * m2) << tsh];
-        }
-        __syncthreads();
-    }
-}
-
-// Stage B: rows {j1, P1 - j1} of a tile: P2-point FFTs, the spectral step with
-// mu (col_base + c is kMulTau2's x-frequency), inverse FFTs, inverse twiddle;
-// in place in Y (and the second output set in Y2 for kMulLam2).
-template <typename W>
-FDE_NI void col4_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W> mu, cx<W>* Y, cx<W>* Y2) {
-    const Col4 g = col4_geom(I);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
-    const cx<W>* gt = tw_global_table<W>(wk.tw);
-    const int tsh = wk.tw.logTW - g.logNp;
-    const bool two = mu.kind == kMulLam2;
-    const int runits = g.P1 / 2 + 1;
-    const int units = g.tiles * runits;
-    const int nt = blockDim.x;
-    const int c = threadIdx.x & (kColTile - 1);
-    const int L2 = 2 * kColTile;                    // lines of one output set
-    const int o2 = L2 * g.ls2;                      // flat origin of the second set
-    for (int un = t.rank; un < units; un += t.size) {
-        const int tile = un / runits, u = un - tile * runits;
-        int rows[2], nrows;
-        split_row_unit(u, g.P1, rows, nrows);
-        const int row0 = rows[0], row1 = rows[1];
-        const long long cb = (long long)tile * kColTile + c;
-        // line (slot, c) holds row rows[slot]; element m2
-        const int total = 2 * g.P2 * kColTile;
-        for (int idx = threadIdx.x; idx < total; idx += nt) {
-            const int r = idx >> 5;
-            const int m2 = r & (g.P2 - 1), slot = r >> g.logP2;
-            cx<W> v = mk(W(0), W(0));
-            if (slot < nrows) v = ldw(Y + ((long long)(slot ? row1 : row0) * g.P2 + m2) * g.n1p + cb);
-            buf[pad((slot * kColTile + c) * g.ls2 + m2)] = v;
-        }
-        __syncthreads();
-        fft_lines<W, false>(buf, g.logP2, L2, g.ls2, wk.tw);
-        // pairs (j, Np - j): element j2 of row rows[0] with element j2m of row
-        // rows[sm]
-        const int npairs = u == 0 ? g.P2 / 2 + 1 : (u == 1 ? g.P2 / 2 : g.P2);
-        const int sm = u >= 2 ? 1 : 0;
-        for (int idx = threadIdx.x; idx < npairs * kColTile; idx += nt) {
-            const int j2 = idx >> 5;
-            const int j2m = u == 0 ? ((g.P2 - j2) & (g.P2 - 1)) : g.P2 - 1 - j2;
-            const int j = row0 + g.P1 * j2;
-            const cx<W> wj = tw_L<W>(wk.tw, j, g.logNp + 1);
-            const int ia = c * g.ls2 + j2, ib = (sm * kColTile + c) * g.ls2 + j2m;
-            cx<W> a, bb, al, be, al2, be2;
-            unpack_pair(buf[pad(ia)], buf[pad(ib)], wj, a, bb);
-            // padding columns (c >= n1) carry zeros; their x-frequency is clamped
-            // to a valid multiplier index
-            const int xc = tile * kColTile + c < g.n1 ? tile * kColTile + c : g.n1 - 1;
-            mu.apply(j, xc, a, bb, al, be, al2, be2);
-            cx<W> Qj, Qm;
-            repack_pair(al, be, wj, Qj, Qm);
-            buf[pad(ia)] = Qj;
-            if (ib != ia) buf[pad(ib)] = Qm;
-            if (two) {
-                repack_pair(al2, be2, wj, Qj, Qm);
-                buf[pad(o2 + ia)] = Qj;
-                if (ib != ia) buf[pad(o2 + ib)] = Qm;
-            }
-        }
-        __syncthreads();
-        fft_lines<W, true>(buf, g.logP2, two ? 2 * L2 : L2, g.ls2, wk.tw);
-        for (int idx = threadIdx.x; idx < total; idx += nt) {
-            const int r = idx >> 5;
-            const int m2 = r & (g.P2 - 1), slot = r >> g.logP2;
-            if (slot >= nrows) continue;
-            const int j1 = slot ? row1 : row0;
-            const cx<W> w = conj(gt[(j1 * m2) << tsh]);
-            const long long at = ((long long)j1 * g.P2 + m2) * g.n1p + cb;
-            const int li = (slot * kColTile + c) * g.ls2 + m2;
-            Y[at] = buf[pad(li)] * w;
-            if (two) Y2[at] = buf[pad(o2 + li)] * w;
-        }
-        __syncthreads();
-    }
-}
-
-// Stage C: inverse P1-point FFTs of each m2 group's lines (both sets when two)
-// and the real outputs a_k (b_k) of rows k - 1 = 2m + e - 1: stored to out
-// (pitch n1) when EPI is false, else through epi (its operands fetched for
-// kUnpackUnroll elements before any of them is stored).
-template <typename W, bool TWO, bool EPI>
-FDE_NI void col4_inv(const Team& t, const Inst& I, const Wk& wk, int G, const cx<W>* Y, const cx<W>* Y2, W* out,
-                     const Epi<W> epi) {
-    const Col4 g = col4_geom(I);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
-    const int groups = g.P2 / G;
-    const int units = g.tiles * groups;
-    const int nt = blockDim.x;
-    const int c = threadIdx.x & (kColTile - 1);
-    const int nl = G * kColTile;
-    const int o2 = nl * g.ls1;
-    const int total = G * g.P1 * kColTile;
-    const int outs = G * (g.P1 / 2) * 2 * kColTile;
-    for (int un = t.rank; un < units; un += t.size) {
-        const int tile = un / groups, m2b = (un - tile * groups) * G;
-        const int col = tile * kColTile + c;
-        for (int idx = threadIdx.x; idx < total; idx += nt) {
-            const int r = idx >> 5;
-            const int j1 = r & (g.P1 - 1), gg = r >> g.logP1;
-            const long long at = ((long long)j1 * g.P2 + m2b + gg) * g.n1p + (long long)tile * kColTile + c;
-            const int li = (gg * kColTile + c) * g.ls1 + j1;
-            buf[pad(li)] = ldw(Y + at);
-            if (TWO) buf[pad(o2 + li)] = ldw(Y2 + at);
-        }
-        __syncthreads();
-        fft_lines<W, true>(buf, g.logP1, TWO ? 2 * nl : nl, g.ls1, wk.tw);
-        // outputs: element m1 < P1/2 of line (gg, c) carries rows 2m - 1 and 2m
-        // (k = 2m, 2m + 1), m = P2 m1 + m2
-        constexpr int U = kUnpackUnroll;
-        for (int base = threadIdx.x; base < outs; base += U * nt) {
-            typename Epi<W>::Ops ops[U];
-            W va[U], vb[U];
-            long long at[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                at[u] = -1;
-                const int idx = base + u * nt;
-                if (idx < outs && col < g.n1) {
-                    const int r = idx >> 5;
-                    const int e = r & 1, q = r >> 1;
-                    const int m1 = q & (g.P1 / 2 - 1), gg = q >> (g.logP1 - 1);
-                    const int k = 2 * (g.P2 * m1 + m2b + gg) + e;
-                    if (k >= 1 && k <= g.n2) {
-                        at[u] = (long long)(k - 1) * g.n1 + col;
-                        if (EPI) ops[u] = epi.fetch(at[u]);
-                        const int li = (gg * kColTile + c) * g.ls1 + m1;
-                        const cx<W> z = buf[pad(li)];
-                        va[u] = e ? z.y : z.x;
-                        vb[u] = W(0);
-                        if (TWO) {
-                            const cx<W> z2 = buf[pad(o2 + li)];
-                            vb[u] = e ? z2.y : z2.x;
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (at[u] < 0) continue;
-                if (EPI) epi.put(at[u], va[u], vb[u], ops[u]);
-                else out[at[u]] = va[u];
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// tau^{-1} along columns in place (z[:, c] <- S2 diag(phi) S2 z[:, c]) as the
-// three stages; false if a barrier timed out.
-template <typename W>
-FDE_NI bool col4_tau(const Team& t, const Inst& I, const Wk& wk, W* z, int G) {
-    cx<W>* Y = reinterpret_cast<cx<W>*>(I.col4);
-    col4_fwd<W, kExtOdd>(t, I, wk, G, Y, z, W(1));
-    if (!team_sync(t)) return false;
-    col4_rows<W>(t, I, wk, mult_tau2<W>(I), Y, nullptr);
-    if (!team_sync(t)) return false;
-    col4_inv<W, false, false>(t, I, wk, G, Y, nullptr, z, Epi<W>{});
-    return true;
-}
-
-// y part of the matvec on the columns of s x, epilogue epi(o, a, b), as the
-// three stages; false if a barrier timed out.
-template <typename W>
-FDE_NI bool col4_matvec(const Team& t, const Inst& I, const Wk& wk, const W* x, W s, Epi<W> epi, int G) {
-    const Col4 g = col4_geom(I);
-    cx<W>* Y = reinterpret_cast<cx<W>*>(I.col4);
-    cx<W>* Y2 = Y + (long long)g.Np * g.n1p;
-    col4_fwd<W, kExtZero>(t, I, wk, G, Y, x, s);
-    if (!team_sync(t)) return false;
-    col4_rows<W>(t, I, wk, mult_matvec<W>(I.ax[1], I.symy), Y, Y2);
-    if (!team_sync(t)) return false;
-    if (I.symy) col4_inv<W, false, true>(t, I, wk, G, Y, Y2, nullptr, epi);
-    else col4_inv<W, true, true>(t, I, wk, G, Y, Y2, nullptr, epi);
-    return true;
-}
-
 // x part of the matvec on the rows of s x; epi(o, a, b).
 template <typename W>
 FDE_NI void plane_matvec_rows(const Team& t, const Inst& I, const Wk& wk, const W* x, W s, Epi<W> epi) {
@@ -1117,20 +844,15 @@ FDE_NI void plane_matvec_cols(const Team& t, const Inst& I, const Wk& wk, const 
 }
 
 
-// The column phases: the four-step layout where it applies, else whole
-// column lines per CTA.
+// The column phases: whole column lines per CTA.
 template <typename W>
 FDE_D bool plane_cols_tau(const Team& t, const Inst& I, const Wk& wk, W* z) {
-    const int G = col4_group<W>(I, wk.bytes, 1);
-    if (G > 0) return col4_tau<W>(t, I, wk, z, G);
     plane_tau_cols<W>(t, I, wk, z);
     return true;
 }
 
 template <typename W>
 FDE_D bool plane_cols_matvec(const Team& t, const Inst& I, const Wk& wk, const W* x, W s, Epi<W> epi) {
-    const int G = col4_group<W>(I, wk.bytes, I.symy ? 1 : 2);
-    if (G > 0) return col4_matvec<W>(t, I, wk, x, s, epi, G);
     plane_matvec_cols<W>(t, I, wk, x, s, epi);
     return true;
 }
