@@ -95,7 +95,9 @@ typedef struct {
     double tol;            /* stop when ||b - A x||_2 <= tol ||b||_2 (right precond.) */
     int max_iters;         /* cap on products with M (inner iterations), >= 1 */
     int precision;         /* fde_precision */
-    double inner_tol;      /* FDE_PREC_F32_IR: relative tolerance of each inner solve; an
+    double inner_tol;      /* FDE_PREC_F32_IR: relative tolerance of each inner solve,
+                              loosened to min(0.5, 0.3 tol ||b|| / ||r||) when that is larger
+                              (the last correction closes only the remaining gap); an
                               inner solve also stops after 2m products (GMRES(m)) or 50
                               (PCG), and the refinement loop then measures the correction
                               by how much it shrank the FP64 residual */

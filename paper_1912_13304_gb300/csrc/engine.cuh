@@ -131,7 +131,14 @@ FDE_D bool run_solve(const Team& t, const Inst& I, const EngineArgs& a, int idx,
                 // iterations only chase rounding noise (about 900 for alpha = 1.8 at
                 // n = 65535).  Its correction goes to the contraction test above.
                 const int cap = st.iterations + (I.method == FDE_GMRES ? 2 * I.restart : kInnerPcgIters);
-                SolveParams sp{a.inner_tol, cap < a.max_iters ? cap : a.max_iters, a.side, 1};
+                // A residual already within a modest factor of the target needs a
+                // correction that closes only that gap (with a margin of 3): solving
+                // it to inner_tol spends iterations on accuracy the refinement
+                // discards.  At most a halving is asked of any correction.
+                double itol = a.inner_tol;
+                const double need = 0.3 * a.tol * nb / rn;
+                if (need > itol) itol = need < 0.5 ? need : 0.5;
+                SolveParams sp{itol, cap < a.max_iters ? cap : a.max_iters, a.side, 1};
                 if (!krylov_core<float>(t, I, lm_f32(I), rhs32, sol32, sp, in, ks, wk)) return false;
                 st.iterations = in.iterations;
                 st.restarts += in.restarts;

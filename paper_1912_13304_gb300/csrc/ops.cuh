@@ -645,6 +645,36 @@ FDE_HD int plane_lines_per_unit(int Np, int nbuf, int nlines_total, int team_siz
     return b < 1 ? 1 : b;
 }
 
+// Rows row0 .. row0 + nb - 1 of a plane (pitch n1, flat origin o0 = row0 n1)
+// from the sine sums in sv (line l at l Np, entry p + 1): out[o] = sv (*
+// post[o]), written back to sv too when BACK.  Every thread loads the post
+// factors of kPackUnroll elements before any store (a store could alias
+// post, so the compiler would not hoist the next load above it).
+template <typename W, bool BACK>
+FDE_D void rows_from_sv(W* sv, int nb, int n1, int Np, long long o0, const W* post, W* out) {
+    constexpr int U = kPackUnroll<W>;
+    const int total = nb * n1;
+    const int nt = blockDim.x;
+    for (int base = threadIdx.x; base < total; base += U * nt) {
+        W f[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * nt;
+            f[u] = (post != nullptr && idx < total) ? __ldg(post + o0 + idx) : W(1);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * nt;
+            if (idx < total) {
+                const int l = idx / n1, p = idx - l * n1;
+                const W v = sv[l * Np + p + 1] * f[u];
+                if (BACK) sv[l * Np + p + 1] = v;
+                out[o0 + idx] = v;
+            }
+        }
+    }
+}
+
 // Lone DST-I along rows: out[row, j-1] = s_j (* post) of the rows of u.
 template <typename W>
 FDE_NI void plane_dst_rows(const Team& t, const Inst& I, const Wk& wk, Combo<W> u, const W* post, W* out) {
@@ -665,13 +695,7 @@ FDE_NI void plane_dst_rows(const Team& t, const Inst& I, const Wk& wk, Combo<W> 
         trace_mark(t, 86);
         cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
         trace_mark(t, 87);
-        for (int idx = threadIdx.x; idx < nb * n1; idx += blockDim.x) {
-            const int l = idx / n1, p = idx - l * n1;
-            const long long o = (long long)(row0 + l) * n1 + p;
-            W v = sv[l * Np + p + 1];
-            if (post) v *= __ldg(post + o);
-            out[o] = v;
-        }
+        rows_from_sv<W, false>(sv, nb, n1, Np, (long long)row0 * n1, post, out);
         __syncthreads();
     }
 }
@@ -764,14 +788,7 @@ FDE_NI void plane_dst_matvec_rows(const Team& t, const Inst& I, const Wk& wk, co
         trace_mark(t, 90);
         cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
         trace_mark(t, 91);
-        for (int idx = threadIdx.x; idx < nb * n1; idx += blockDim.x) {
-            const int l = idx / n1, p = idx - l * n1;
-            const long long o = (long long)(row0 + l) * n1 + p;
-            W v = sv[l * Np + p + 1];
-            if (post) v *= __ldg(dinv + o);
-            sv[l * Np + p + 1] = v;
-            z[o] = v;
-        }
+        rows_from_sv<W, true>(sv, nb, n1, Np, (long long)row0 * n1, post ? dinv : nullptr, z);
         __syncthreads();
         trace_mark(t, 92);
         cta_pack<W, kExtZero, false>(buf, nb, n1, Np, [&](int l, int k, bool) { return sv[l * Np + k]; });
