@@ -40,6 +40,27 @@ template <typename R> FDE_HD cx<R> mul_mi(cx<R> a) { return mk(a.y, -a.x); }    
 template <typename R> FDE_HD cx<R> czero() { return mk(R(0), R(0)); }
 template <typename R> FDE_HD cx<R> cvt(cx<double> a) { return mk(R(a.x), R(a.y)); }
 
+// Threads of a CTA that work and synchronise together: the whole CTA
+// (barrier 0, the one __syncthreads uses), or one of its two halves (warps
+// 0-7 or 8-15 of 512 threads, named barriers 1 and 2), whose phases then
+// interleave on the SM: one half's global loads overlap the other's FFT.
+struct Grp {
+    int tid;    // thread index within the group
+    int nt;     // threads in the group (a multiple of 32)
+    int bar;    // hardware barrier id
+};
+FDE_D Grp grp_cta() { return Grp{(int)threadIdx.x, (int)blockDim.x, 0}; }
+FDE_D Grp grp_half(int h) {
+    const int nt = (int)blockDim.x / 2;
+    return Grp{(int)threadIdx.x - h * nt, nt, 1 + h};
+}
+// Every thread of the group executes the same sequence of grp_sync calls
+// (all loops over units and lines have group-uniform bounds).
+FDE_D void grp_sync(const Grp& g) {
+    if (g.bar == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(g.bar), "r"(g.nt) : "memory");
+}
+
 FDE_HD int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
 
 // Symbol data of one axis.  Np = n + 1 (a power of two) is the length of the

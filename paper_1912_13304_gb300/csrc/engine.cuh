@@ -219,14 +219,23 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
         if (team_id >= nteams) return;
         first = team_id * ts;
     }
-    Team t;
-    t.rank = blockIdx.x - first;
-    t.size = ts;
-    t.count = &a.sync->bar_count[team_id];
-    t.gen = &a.sync->bar_gen[team_id];
-    t.partial = a.sync->partial + (size_t)first * kMaxDots;
-    t.abort_flag = &a.sync->abort_flag;
-    t.sync = a.sync;
+    // per-CTA constants in shared memory: functions reach them through
+    // references, which for a thread-local object would be stack (local
+    // memory) loads that miss the small L1 left beside the work area
+    __shared__ Team s_team;
+    __shared__ Wk s_wk;
+    __shared__ KShared s_ks;
+    if (threadIdx.x == 0) {
+        s_team.rank = blockIdx.x - first;
+        s_team.size = ts;
+        s_team.count = &a.sync->bar_count[team_id];
+        s_team.gen = &a.sync->bar_gen[team_id];
+        s_team.partial = a.sync->partial + (size_t)first * kMaxDots;
+        s_team.abort_flag = &a.sync->abort_flag;
+        s_team.sync = a.sync;
+    }
+    __syncthreads();
+    const Team& t = s_team;
     int next_static = team_id;
     while (true) {
         int idx;
@@ -250,15 +259,29 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
         __syncthreads();
         const int m = s_inst.method == FDE_GMRES ? s_inst.restart : 1;
         const size_t hdr = kshared_bytes(m, s_inst.logTsm);
-        KShared ks = kshared_carve(dsm, m);
-        ks.wide = reinterpret_cast<double*>(dsm + hdr);
+        if (threadIdx.x == 0) {
+            KShared k = kshared_carve(dsm, m);
+            k.wide = reinterpret_cast<double*>(dsm + hdr);
+            k.twq32 = reinterpret_cast<cx<float>*>(k.twq + padded_len((1 << s_inst.logTsm) >> 2));
+            s_ks = k;
+            s_wk.smem = dsm + hdr;
+            s_wk.bytes = a.smem_bytes - (int)hdr;
+            s_wk.tw.q = k.twq;
+            s_wk.tw.q32 = k.twq32;
+            s_wk.tw.logT = s_inst.logTsm;
+            s_wk.tw.g64 = s_inst.tw64;
+            s_wk.tw.g32 = s_inst.tw32;
+            s_wk.tw.logTW = s_inst.logTW;
+        }
+        __syncthreads();
+        KShared& ks = s_ks;
+        const Wk& wk = s_wk;
         // quarter-wave twiddle table of W_T, T = 2^logTsm, from the global table;
         // entry i at pad(i), so the strided lookups of the later radix passes
         // (index r k 2^s) spread over the banks
         {
             const int q = (1 << s_inst.logTsm) >> 2;
             const int sh = s_inst.logTW - s_inst.logTsm;
-            ks.twq32 = reinterpret_cast<cx<float>*>(ks.twq + padded_len(q));
             for (int i = threadIdx.x; i < q; i += blockDim.x) {
                 const cx<double> w = s_inst.tw64[i << sh];
                 ks.twq[pad(i)] = w;
@@ -266,15 +289,6 @@ __global__ void __launch_bounds__(kThreads, 1) fde_engine(const __grid_constant_
             }
         }
         __syncthreads();
-        Wk wk;
-        wk.smem = dsm + hdr;
-        wk.bytes = a.smem_bytes - (int)hdr;
-        wk.tw.q = ks.twq;
-        wk.tw.q32 = ks.twq32;
-        wk.tw.logT = s_inst.logTsm;
-        wk.tw.g64 = s_inst.tw64;
-        wk.tw.g32 = s_inst.tw32;
-        wk.tw.logTW = s_inst.logTW;
         bool ok;
         if (a.op == kOpSolve) ok = run_solve<MODE>(t, s_inst, a, inst_i, ks, wk);
         else ok = run_op<MODE>(t, s_inst, a, inst_i, wk);

@@ -116,7 +116,7 @@ FDE_D void dft8(cx<R>* v) {
 }
 
 // a W_16^E (forward) or a W_16^-E (inverse), W_16 = exp(-2 pi i / 16), for the
-// exponents that the 4 x 4 split of a 16-point DFT needs.
+// exponents that the 4 x 4 split of a 16-point DFT needs (radix16_item).
 template <typename R, bool INV, int E>
 FDE_D cx<R> w16(cx<R> a) {
     const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173), h = R(0.70710678118654752440);
@@ -130,42 +130,11 @@ FDE_D cx<R> w16(cx<R> a) {
     return mk(a.x * wr - a.y * wi, a.x * wi + a.y * wr);
 }
 
-// 16-point DFT as 4 x 4: DFT4 over n1 of x[4 n1 + n2] for each n2, twiddle
-// W_16^(n2 k1), DFT4 over n2 for each k1; output X[k1 + 4 k2] in natural order.
-template <typename R, bool INV>
-FDE_D void dft16(cx<R>* v) {
-    cx<R> y[4][4];
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) {
-        cx<R> t[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
-        dft4<R, INV>(t);
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) y[k1][n2] = t[k1];
-    }
-    y[1][1] = w16<R, INV, 1>(y[1][1]);
-    y[1][2] = w16<R, INV, 2>(y[1][2]);
-    y[1][3] = w16<R, INV, 3>(y[1][3]);
-    y[2][1] = w16<R, INV, 2>(y[2][1]);
-    y[2][2] = rot_quarter<R, INV>(y[2][2]);
-    y[2][3] = w16<R, INV, 6>(y[2][3]);
-    y[3][1] = w16<R, INV, 3>(y[3][1]);
-    y[3][2] = w16<R, INV, 6>(y[3][2]);
-    y[3][3] = w16<R, INV, 9>(y[3][3]);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-        cx<R> t[4] = {y[k1][0], y[k1][1], y[k1][2], y[k1][3]};
-        dft4<R, INV>(t);
-#pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
-    }
-}
-
 template <typename R, int RAD, bool INV>
 FDE_D void dft_reg(cx<R>* v) {
     if constexpr (RAD == 2) dft2<R, INV>(v[0], v[1]);
     else if constexpr (RAD == 4) dft4<R, INV>(v);
-    else if constexpr (RAD == 8) dft8<R, INV>(v);
-    else dft16<R, INV>(v);
+    else dft8<R, INV>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -175,9 +144,65 @@ FDE_D void dft_reg(cx<R>* v) {
 // writes y[(j - k) RAD + k + r Ns].
 // ---------------------------------------------------------------------------
 
+// One radix-16 item, column by column of the 4 x 4 split (r = n2 + 4 n1): the
+// four inputs of column n2 are loaded, twiddled by w^(r k) and transformed
+// (DFT4 over n1) before the next column's loads, so at most the 16 partial
+// results, one column's inputs and the base twiddles are live (no spills in
+// a kernel of 128 registers, against 19 local loads per item when the 16
+// inputs were loaded first).  The twiddle powers are products of w, w^2, w^4
+// and w^8 from the table, at most three roundings each.  Output X[k1 + 4 k2]
+// lands in y[k1 + 4 k2].
+template <typename R, bool INV>
+FDE_D void radix16_item(const cx<R>* buf, int o, int logItems, int k, bool tw_on, int twsh, bool smem_tw,
+                        const Tw& tw, const cx<R>* gtab, cx<R>* y) {
+    auto look = [&](int e) {
+        const int idx = (e * k) << twsh;
+        const cx<R> w = smem_tw ? tw_quarter<R>(tw, idx) : gtab[idx];
+        return INV ? conj(w) : w;
+    };
+    cx<R> w1 = mk(R(1), R(0)), w2 = w1, w4 = w1, w8 = w1;
+    if (tw_on) { w1 = look(1); w2 = look(2); w4 = look(4); w8 = look(8); }
+    const cx<R> w12 = w4 * w8;
+    cx<R> c[4][4];                           // c[k1][n2]
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        cx<R> t4[4];
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) t4[n1] = buf[pad(o + ((n2 + 4 * n1) << logItems))];
+        if (tw_on) {
+            cx<R> wb = w1;                   // w^n2
+            if (n2 == 2) wb = w2;
+            if (n2 == 3) wb = w1 * w2;
+            if (n2 > 0) t4[0] = t4[0] * wb;
+            t4[1] = t4[1] * (n2 > 0 ? wb * w4 : w4);
+            t4[2] = t4[2] * (n2 > 0 ? wb * w8 : w8);
+            t4[3] = t4[3] * (n2 > 0 ? wb * w12 : w12);
+        }
+        dft4<R, INV>(t4);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) c[k1][n2] = t4[k1];
+    }
+    c[1][1] = w16<R, INV, 1>(c[1][1]);
+    c[1][2] = w16<R, INV, 2>(c[1][2]);
+    c[1][3] = w16<R, INV, 3>(c[1][3]);
+    c[2][1] = w16<R, INV, 2>(c[2][1]);
+    c[2][2] = rot_quarter<R, INV>(c[2][2]);
+    c[2][3] = w16<R, INV, 6>(c[2][3]);
+    c[3][1] = w16<R, INV, 3>(c[3][1]);
+    c[3][2] = w16<R, INV, 6>(c[3][2]);
+    c[3][3] = w16<R, INV, 9>(c[3][3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        cx<R> t4[4] = {c[k1][0], c[k1][1], c[k1][2], c[k1][3]};
+        dft4<R, INV>(t4);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = t4[k2];
+    }
+}
+
 template <typename R, int RAD, int EPT, bool INV>
-FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, int logNs, const Tw& tw,
-                                 bool smem_tw) {
+FDE_D void stockham_pass_inplace(const Grp& g, cx<R>* buf, int logP, int nlines, int lstride, int logNs,
+                                 const Tw& tw, bool smem_tw) {
     constexpr int K = EPT / RAD;                // items per thread
     constexpr int LR = RAD == 16 ? 4 : (RAD == 8 ? 3 : (RAD == 4 ? 2 : 1));
     const int logItems = logP - LR;             // items per line = P / RAD
@@ -188,46 +213,18 @@ FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, 
     cx<R> v[K][RAD];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        const int it = threadIdx.x + t * blockDim.x;
+        const int it = g.tid + t * g.nt;
         if (it < total) {
             const int line = it >> logItems;
             const int j = it & ((1 << logItems) - 1);
             const int base = line * lstride;
             const int k = j & (Ns - 1);
+            if constexpr (RAD == 16) {
+                radix16_item<R, INV>(buf, base + j, logItems, k, Ns > 1, twsh, smem_tw, tw, gtab, v[t]);
+            } else {
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) v[t][r] = buf[pad(base + j + (r << logItems))];
-            if (Ns > 1) {
-                if constexpr (RAD == 16) {
-                    // w^1, w^2, w^4, w^8 from the table, the other powers as
-                    // products of those (at most three roundings each), each
-                    // applied as soon as it is formed
-                    auto look = [&](int e) {
-                        const int idx = (e * k) << twsh;
-                        const cx<R> w = smem_tw ? tw_quarter<R>(tw, idx) : gtab[idx];
-                        return INV ? conj(w) : w;
-                    };
-                    const cx<R> w1 = look(1), w2 = look(2), w4 = look(4), w8 = look(8);
-                    cx<R>* x = v[t];
-                    x[1] = x[1] * w1;
-                    x[2] = x[2] * w2;
-                    x[4] = x[4] * w4;
-                    x[8] = x[8] * w8;
-                    x[9] = x[9] * (w1 * w8);
-                    x[10] = x[10] * (w2 * w8);
-                    x[12] = x[12] * (w4 * w8);
-                    const cx<R> w3 = w1 * w2;
-                    x[3] = x[3] * w3;
-                    x[11] = x[11] * (w3 * w8);
-                    const cx<R> w5 = w1 * w4;
-                    x[5] = x[5] * w5;
-                    x[13] = x[13] * (w5 * w8);
-                    const cx<R> w6 = w2 * w4;
-                    x[6] = x[6] * w6;
-                    x[14] = x[14] * (w6 * w8);
-                    const cx<R> w7 = w3 * w4;
-                    x[7] = x[7] * w7;
-                    x[15] = x[15] * (w7 * w8);
-                } else {
+                for (int r = 0; r < RAD; ++r) v[t][r] = buf[pad(base + j + (r << logItems))];
+                if (Ns > 1) {
 #pragma unroll
                     for (int r = 1; r < RAD; ++r) {
                         const int idx = (r * k) << twsh;
@@ -236,14 +233,14 @@ FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, 
                         v[t][r] = v[t][r] * w;
                     }
                 }
+                dft_reg<R, RAD, INV>(v[t]);
             }
-            dft_reg<R, RAD, INV>(v[t]);
         }
     }
-    __syncthreads();
+    grp_sync(g);
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        const int it = threadIdx.x + t * blockDim.x;
+        const int it = g.tid + t * g.nt;
         if (it < total) {
             const int line = it >> logItems;
             const int j = it & ((1 << logItems) - 1);
@@ -253,12 +250,13 @@ FDE_D void stockham_pass_inplace(cx<R>* buf, int logP, int nlines, int lstride, 
             for (int r = 0; r < RAD; ++r) buf[pad(dst + r * Ns)] = v[t][r];
         }
     }
-    __syncthreads();
+    grp_sync(g);
 }
 
 // In-place FFT of nlines lines held in (padded) shared memory, every pass
 // one radix item per thread (registers hold RAD values), so a call requires
-// nlines * P / RAD <= kFftItems<R> * blockDim.x for the smallest radix it uses.
+// nlines * P / RAD <= kFftItems<R> * (threads of the group) for the smallest
+// radix it uses.
 //
 // Radix items per thread and pass.  One: two items per thread (measured for
 // FP32 with 512 threads, and for both precisions with 256 threads and twice
@@ -301,7 +299,7 @@ FDE_HD unsigned fft_schedule(int logP, int elem_bytes) {
 }
 
 template <typename R, bool INV>
-FDE_D void fft_inplace(cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
+FDE_D void fft_inplace(const Grp& g, cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
     constexpr int K = kFftItems<R>;
     const bool smem_tw = logP <= tw.logT;
     int logNs = 0;
@@ -309,14 +307,14 @@ FDE_D void fft_inplace(cx<R>* buf, int logP, int nlines, int lstride, const Tw& 
         const int lr = (int)(s & 15u);
         if constexpr (sizeof(R) == 4) {
             if (lr == 4) {
-                stockham_pass_inplace<R, 16, 16 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+                stockham_pass_inplace<R, 16, 16 * K, INV>(g, buf, logP, nlines, lstride, logNs, tw, smem_tw);
                 logNs += 4;
                 continue;
             }
         }
-        if (lr == 3) stockham_pass_inplace<R, 8, 8 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
-        else if (lr == 2) stockham_pass_inplace<R, 4, 4 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
-        else stockham_pass_inplace<R, 2, 2 * K, INV>(buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        if (lr == 3) stockham_pass_inplace<R, 8, 8 * K, INV>(g, buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        else if (lr == 2) stockham_pass_inplace<R, 4, 4 * K, INV>(g, buf, logP, nlines, lstride, logNs, tw, smem_tw);
+        else stockham_pass_inplace<R, 2, 2 * K, INV>(g, buf, logP, nlines, lstride, logNs, tw, smem_tw);
         logNs += lr;
     }
 }
@@ -339,15 +337,23 @@ FDE_HD int fft_lines_per_call(int logP, int threads, int elem_bytes) {
 // lstride), which commutes with pad() because lstride is a multiple of 16
 // whenever more than one batch is needed.  A single line with more radix
 // items than kFftItems<R> per thread is not supported (callers split such
-// lines).  Not inlined: the radix passes then get the whole register budget
-// of the thread instead of what a calling phase with much live state leaves.
+// lines).
 template <typename R, bool INV>
-FDE_NI void fft_lines(cx<R>* buf, int logP, int nlines, int lstride, const Tw tw) {
-    const int cap = fft_lines_per_call(logP, blockDim.x, (int)sizeof(R));
+FDE_D void fft_lines_in(const Grp& g, cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
+    const int cap = fft_lines_per_call(logP, g.nt, (int)sizeof(R));
     for (int l0 = 0; l0 < nlines; l0 += cap) {
         const int nl = (nlines - l0) < cap ? (nlines - l0) : cap;
-        fft_inplace<R, INV>(buf + pad(l0 * lstride), logP, nl, lstride, tw);
+        fft_inplace<R, INV>(g, buf + pad(l0 * lstride), logP, nl, lstride, tw);
     }
+}
+
+// The same, not inlined: the radix passes get the thread's registers, at the
+// price of the register saves of a call.  Callers with a spectral step
+// between two transforms use the fused calls of the line layer instead, which
+// pay that price once.
+template <typename R, bool INV>
+FDE_NI void fft_lines(const Grp g, cx<R>* buf, int logP, int nlines, int lstride, const Tw& tw) {
+    fft_lines_in<R, INV>(g, buf, logP, nlines, lstride, tw);
 }
 
 // Ping-pong variant for one long line in global memory (one CTA, symbol

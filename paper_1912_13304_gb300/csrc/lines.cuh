@@ -150,13 +150,13 @@ template <typename W> constexpr int kPackUnroll = sizeof(W) == 4 ? 8 : 4;
 constexpr int kUnpackUnroll = 4;
 
 template <typename W, int EXT, bool COLMAJOR, typename GetF>
-FDE_D void cta_pack(cx<W>* buf, int B, int n, int Np, GetF get) {
+FDE_D void cta_pack(const Grp& g, cx<W>* buf, int B, int n, int Np, GetF get) {
     constexpr int kUnroll = kPackUnroll<W>;
     const int logNp = log2_pow2(Np);
     const int total = B << logNp;
-    const int nt = blockDim.x;
-    Walk w(COLMAJOR, threadIdx.x, nt, B, logNp);
-    for (int base = threadIdx.x; base < total; base += kUnroll * nt) {
+    const int nt = g.nt;
+    Walk w(COLMAJOR, g.tid, nt, B, logNp);
+    for (int base = g.tid; base < total; base += kUnroll * nt) {
         cx<W> v[kUnroll];
         int at[kUnroll];
 #pragma unroll
@@ -174,17 +174,17 @@ FDE_D void cta_pack(cx<W>* buf, int B, int n, int Np, GetF get) {
         for (int u = 0; u < kUnroll; ++u)
             if (at[u] >= 0) buf[pad(at[u])] = v[u];
     }
-    __syncthreads();
+    grp_sync(g);
 }
 
 // Pairs (j, Np - j) of B lines, j = 0..Np/2: f(l, j) per pair, no division
 // per pair (Np >= 2, a power of two).
 template <typename F>
-FDE_D void cta_pairs(int B, int logNp, F f) {
+FDE_D void cta_pairs(const Grp& g, int B, int logNp, F f) {
     const int lh = logNp - 1;
     const int hm = 1 << lh;
     const int total = B << lh;
-    for (int idx = threadIdx.x; idx < total + B; idx += blockDim.x) {
+    for (int idx = g.tid; idx < total + B; idx += g.nt) {
         if (idx < total) f(idx >> lh, idx & (hm - 1));
         else f(idx - total, hm);
     }
@@ -193,10 +193,10 @@ FDE_D void cta_pairs(int B, int logNp, F f) {
 // Spectral step on all pairs of B lines; the second output (kMulLam2) goes
 // to lines B..2B-1.  col_of_line gives kMulTau2's x-frequency of a line.
 template <typename W, typename ColF>
-FDE_D void cta_spectral(cx<W>* buf, int B, int Np, int logNp, const Tw& tw, const Mult<W>& mu,
+FDE_D void cta_spectral(const Grp& g, cx<W>* buf, int B, int Np, int logNp, const Tw& tw, const Mult<W>& mu,
                         ColF col_of_line) {
     const bool two = mu.kind == kMulLam2;
-    cta_pairs(B, logNp, [&](int l, int j) {
+    cta_pairs(g, B, logNp, [&](int l, int j) {
         const int jm = (Np - j) & (Np - 1);
         const int o = l * Np;
         const cx<W> wj = tw_L<W>(tw, j, logNp + 1);
@@ -214,15 +214,15 @@ FDE_D void cta_spectral(cx<W>* buf, int B, int Np, int logNp, const Tw& tw, cons
             if (jm != j) buf[pad(o2 + jm)] = Qm;
         }
     });
-    __syncthreads();
+    grp_sync(g);
 }
 
 // Lone DST-I of B lines: after the forward FFT of the odd extension, write
 // the unnormalised sine sums s_j = -Im X_j / 2 (j = 1..n) into the real
 // shared-memory array s (B lines at stride Np, unpadded).
 template <typename W>
-FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, const Tw& tw) {
-    cta_pairs(B, logNp, [&](int l, int j) {
+FDE_D void cta_dst_extract(const Grp& g, const cx<W>* buf, W* s, int B, int Np, int logNp, const Tw& tw) {
+    cta_pairs(g, B, logNp, [&](int l, int j) {
         const int jm = (Np - j) & (Np - 1);
         const int o = l * Np;
         cx<W> a, b;
@@ -232,7 +232,27 @@ FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, con
             if (jm != j) s[o + (Np - j)] = W(0.5) * b.y;
         }
     });
-    __syncthreads();
+    grp_sync(g);
+}
+
+// Forward FFT of B lines, the spectral step with mu (kMulTau2's x-frequency
+// of line l is col0 + l) and the inverse FFT of the nout output lines, in
+// one call: the register saves of a non-inlined call are paid once per unit
+// of lines instead of once per transform.
+template <typename W>
+FDE_NI void fft_spectral_lines(const Grp g, cx<W>* buf, int B, int Np, int logNp, const Tw& tw, const Mult<W>& mu,
+                               int col0, int nout) {
+    fft_lines_in<W, false>(g, buf, logNp, B, Np, tw);
+    cta_spectral<W>(g, buf, B, Np, logNp, tw, mu, [&](int l) { return col0 + l; });
+    fft_lines_in<W, true>(g, buf, logNp, nout, Np, tw);
+}
+
+// Forward FFT of the odd extensions of B lines and the sine sums s_j, in one
+// call.
+template <typename W>
+FDE_NI void fft_dst_lines(const Grp g, cx<W>* buf, W* s, int B, int Np, int logNp, const Tw& tw) {
+    fft_lines_in<W, false>(g, buf, logNp, B, Np, tw);
+    cta_dst_extract<W>(g, buf, s, B, Np, logNp, tw);
 }
 
 // Unpack q_m = a_{2m} + i a_{2m+1} and hand a_k (k = 1..n, p = k - 1) to
@@ -240,14 +260,14 @@ FDE_D void cta_dst_extract(const cx<W>* buf, W* s, int B, int Np, int logNp, con
 // The fetches of kUnpackUnroll elements (the epilogue's global loads) are issued
 // before any of their puts, so the loads are in flight together.
 template <typename W, bool COLMAJOR, bool TWO, typename FetchF, typename PutF>
-FDE_D void cta_unpack2(const cx<W>* buf, int B, int n, int Np, FetchF fetch, PutF put) {
+FDE_D void cta_unpack2(const Grp& g, const cx<W>* buf, int B, int n, int Np, FetchF fetch, PutF put) {
     constexpr int kUnroll = kUnpackUnroll;
     const int logNp = log2_pow2(Np);
     const int total = B << logNp;
-    const int nt = blockDim.x;
-    Walk w(COLMAJOR, threadIdx.x, nt, B, logNp);
+    const int nt = g.nt;
+    Walk w(COLMAJOR, g.tid, nt, B, logNp);
     using Ops = decltype(fetch(0, 0));
-    for (int base = threadIdx.x; base < total; base += kUnroll * nt) {
+    for (int base = g.tid; base < total; base += kUnroll * nt) {
         Ops ops[kUnroll];
         W va[kUnroll], vb[kUnroll];
         int li[kUnroll], pi[kUnroll];
@@ -280,8 +300,8 @@ struct NoOps {};
 
 // Unpack with an epilogue that loads nothing: epi(l, p, a_k, b_k).
 template <typename W, bool COLMAJOR, bool TWO, typename EpiF>
-FDE_D void cta_unpack(const cx<W>* buf, int B, int n, int Np, EpiF epi) {
-    cta_unpack2<W, COLMAJOR, TWO>(buf, B, n, Np, [](int, int) { return NoOps{}; },
+FDE_D void cta_unpack(const Grp& g, const cx<W>* buf, int B, int n, int Np, EpiF epi) {
+    cta_unpack2<W, COLMAJOR, TWO>(g, buf, B, n, Np, [](int, int) { return NoOps{}; },
                                   [&](int l, int p, W va, W vb, const NoOps&) { epi(l, p, va, vb); });
 }
 

@@ -76,6 +76,19 @@ FDE_D Mult<W> mult_tau2(const Inst& I) {
 // this way).
 // ---------------------------------------------------------------------------
 
+// A phase's multipliers in a per-CTA shared slot, for the fused transform
+// calls (a reference to a thread-local copy would be a stack address, read
+// back through the small L1 beside the work area).  Every thread of the CTA
+// calls this at the start of a phase.
+template <typename W>
+FDE_D const Mult<W>& mult_slot(const Mult<W>& m) {
+    __shared__ Mult<W> s;
+    __syncthreads();
+    if (threadIdx.x == 0) s = m;
+    __syncthreads();
+    return s;
+}
+
 template <typename W>
 struct Combo {
     const W* base;         // may be null (then 0)
@@ -234,11 +247,10 @@ FDE_NI void cta_tau_1d(const Inst& I, const Wk& wk, Combo<W> u, Epi<W> epi) {
     const W* dinv = Prec<W>::dinv(I);
     if (I.has_D && I.order == FDE_ORDER_D_TAU) u.pre = dinv;
     if (I.has_D && I.order == FDE_ORDER_TAU_D) epi.post = dinv;
-    cta_pack<W, kExtOdd, false>(buf, 1, n, Np, [&](int, int k, bool d) { return u.get(k - 1, d); });
-    fft_lines<W, false>(buf, A.logNp, 1, Np, wk.tw);
-    cta_spectral<W>(buf, 1, Np, A.logNp, wk.tw, mult_tau1<W>(A), [](int) { return 0; });
-    fft_lines<W, true>(buf, A.logNp, 1, Np, wk.tw);
-    cta_unpack2<W, false, false>(buf, 1, n, Np, [&](int, int p) { return epi.fetch(p); },
+    const Mult<W>& mu = mult_slot<W>(mult_tau1<W>(A));
+    cta_pack<W, kExtOdd, false>(grp_cta(), buf, 1, n, Np, [&](int, int k, bool d) { return u.get(k - 1, d); });
+    fft_spectral_lines<W>(grp_cta(), buf, 1, Np, A.logNp, wk.tw, mu, 0, 1);
+    cta_unpack2<W, false, false>(grp_cta(), buf, 1, n, Np, [&](int, int p) { return epi.fetch(p); },
                                  [&](int, int p, W va, W vb, const typename Epi<W>::Ops& r) { epi.put(p, va, vb, r); });
     __syncthreads();
 }
@@ -250,14 +262,13 @@ FDE_NI void cta_matvec_1d(const Inst& I, const Wk& wk, const W* x, W s, Epi<W> e
     const int n = A.n, Np = A.Np;
     cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
     const bool sym = I.symx;
-    cta_pack<W, kExtZero, false>(buf, 1, n, Np, [&](int, int k, bool) { return s * ldw(x + (k - 1)); });
-    fft_lines<W, false>(buf, A.logNp, 1, Np, wk.tw);
-    cta_spectral<W>(buf, 1, Np, A.logNp, wk.tw, mult_matvec<W>(A, sym), [](int) { return 0; });
-    fft_lines<W, true>(buf, A.logNp, sym ? 1 : 2, Np, wk.tw);
+    const Mult<W>& mu = mult_slot<W>(mult_matvec<W>(A, sym));
+    cta_pack<W, kExtZero, false>(grp_cta(), buf, 1, n, Np, [&](int, int k, bool) { return s * ldw(x + (k - 1)); });
+    fft_spectral_lines<W>(grp_cta(), buf, 1, Np, A.logNp, wk.tw, mu, 0, sym ? 1 : 2);
     auto fe = [&](int, int p) { return epi.fetch(p); };
     auto pu = [&](int, int p, W va, W vb, const typename Epi<W>::Ops& r) { epi.put(p, va, vb, r); };
-    if (sym) cta_unpack2<W, false, false>(buf, 1, n, Np, fe, pu);
-    else cta_unpack2<W, false, true>(buf, 1, n, Np, fe, pu);
+    if (sym) cta_unpack2<W, false, false>(grp_cta(), buf, 1, n, Np, fe, pu);
+    else cta_unpack2<W, false, true>(grp_cta(), buf, 1, n, Np, fe, pu);
     __syncthreads();
 }
 
@@ -432,7 +443,7 @@ FDE_NI void split_fwd_cols(const Team& t, const Inst& I, const Wk& wk, Combo<W> 
         }
         __syncthreads();
         trace_mark(t, 50);
-        fft_lines<W, false>(buf, A.logP1, wu, P1, wk.tw);
+        fft_lines<W, false>(grp_cta(), buf, A.logP1, wu, P1, wk.tw);
         trace_mark(t, 51);
         for (int idx = threadIdx.x; idx < wu * P1; idx += blockDim.x) {
             const int c = idx % wu, j1 = idx / wu;
@@ -486,7 +497,7 @@ FDE_NI void split_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>
         }
         __syncthreads();
         trace_mark(t, 41);
-        fft_lines<W, false>(buf, A.logP2, 2 * B, P2, wk.tw);
+        fft_lines<W, false>(grp_cta(), buf, A.logP2, 2 * B, P2, wk.tw);
         trace_mark(t, 42);
         for (int idx = threadIdx.x; idx < B * P2; idx += blockDim.x) {
             const int b = idx / P2, q = idx - b * P2;
@@ -517,7 +528,7 @@ FDE_NI void split_rows(const Team& t, const Inst& I, const Wk& wk, const Mult<W>
         }
         __syncthreads();
         trace_mark(t, 43);
-        fft_lines<W, true>(buf, A.logP2, two ? 4 * B : 2 * B, P2, wk.tw);
+        fft_lines<W, true>(grp_cta(), buf, A.logP2, two ? 4 * B : 2 * B, P2, wk.tw);
         trace_mark(t, 44);
         for (int idx = threadIdx.x; idx < 2 * B * P2; idx += blockDim.x) {
             const int l = idx / P2, m2 = idx - l * P2;
@@ -547,7 +558,7 @@ FDE_D void split_inv_unit_fft(const Inst& I, const Wk& wk, const cx<W>* Y, const
         if (two) buf[pad((cc + c) * P1 + j1)] = ldw(Y2 + (long long)j1 * P2 + m2b + c);
     }
     __syncthreads();
-    fft_lines<W, true>(buf, A.logP1, two ? 2 * cc : cc, P1, wk.tw);
+    fft_lines<W, true>(grp_cta(), buf, A.logP1, two ? 2 * cc : cc, P1, wk.tw);
 }
 
 // Inverse column phase: a_k (and b_k) of each unit's columns to the epilogue.
@@ -622,7 +633,7 @@ FDE_NI void split_tau_inv_mv_fwd(const Team& t, const Inst& I, const Wk& wk, con
         }
         __syncthreads();
         trace_mark(t, 54);
-        fft_lines<W, false>(buf, A.logP1, wu, P1, wk.tw);
+        fft_lines<W, false>(grp_cta(), buf, A.logP1, wu, P1, wk.tw);
         trace_mark(t, 55);
         for (int idx = threadIdx.x; idx < wu * P1; idx += blockDim.x) {
             const int c = idx % wu, j1 = idx / wu;
@@ -638,11 +649,56 @@ FDE_NI void split_tau_inv_mv_fwd(const Team& t, const Inst& I, const Wk& wk, con
 // ---------------------------------------------------------------------------
 
 template <typename W>
-FDE_HD int plane_lines_per_unit(int Np, int nbuf, int nlines_total, int team_size, int bytes, int extra_real) {
+FDE_HD int plane_lines_per_unit(int Np, int nbuf, int nlines_total, int workers, int bytes, int extra_real) {
     const int cap = max_lines<W>(Np, nbuf, bytes, extra_real);
-    const int want = (nlines_total + team_size - 1) / team_size;
+    const int want = (nlines_total + workers - 1) / workers;
     int b = want < cap ? want : cap;
     return b < 1 ? 1 : b;
+}
+
+// Work area of one of ng groups (256-byte aligned).
+FDE_HD int plane_group_bytes(int bytes, int ng) { return (bytes / ng) & ~255; }
+
+// Thread groups per CTA of a plane phase: the two halves when a line with
+// its buffers fits half the work area and the FFT's widest pass fits half
+// the threads (FP32 lines up to 4096 points), else the whole CTA.  While one
+// half waits on the global loads of a pack or an epilogue, the other runs
+// its FFT passes; a whole-CTA phase leaves the SM's pipes idle in turn.
+template <typename W>
+FDE_HD int plane_groups(int Np, int nbuf, int bytes, int extra_real, int threads) {
+    if (fft_lines_per_call(ilog2(Np), threads / 2, (int)sizeof(W)) < 1) return 1;
+    return max_lines<W>(Np, nbuf, plane_group_bytes(bytes, 2), extra_real) >= 1 ? 2 : 1;
+}
+
+// Split of a plane phase over the team: units of B lines; unit un belongs to
+// CTA un mod t.size (as for ng = 1, so a CTA owns the same lines whatever its
+// grouping) and, in that CTA, to group (un / t.size) mod ng.
+struct PlaneSplit {
+    Grp g;
+    unsigned char* smem;    // the group's work area
+    int ng, B, units, first, step;
+};
+
+// Row phases split the CTA; column phases keep it whole, since a column unit
+// of C lines reads C adjacent elements of every row, and halving C halves the
+// useful bytes of every 32-byte sector loaded.
+constexpr bool kRowHalves = true;
+constexpr bool kColHalves = false;
+
+template <typename W>
+FDE_D PlaneSplit plane_split(const Team& t, const Wk& wk, int Np, int nbuf, int nlines, int extra_real,
+                             bool halves) {
+    PlaneSplit ps;
+    ps.ng = halves ? plane_groups<W>(Np, nbuf, wk.bytes, extra_real, (int)blockDim.x) : 1;
+    const int gi = ps.ng == 2 && (int)threadIdx.x >= (int)blockDim.x / 2 ? 1 : 0;
+    ps.g = ps.ng == 2 ? grp_half(gi) : grp_cta();
+    const int gb = plane_group_bytes(wk.bytes, ps.ng);
+    ps.smem = wk.smem + (size_t)gi * gb;
+    ps.B = plane_lines_per_unit<W>(Np, nbuf, nlines, t.size * ps.ng, gb, extra_real);
+    ps.units = (nlines + ps.B - 1) / ps.B;
+    ps.first = t.rank + gi * t.size;
+    ps.step = ps.ng * t.size;
+    return ps;
 }
 
 // Rows row0 .. row0 + nb - 1 of a plane (pitch n1, flat origin o0 = row0 n1)
@@ -651,11 +707,11 @@ FDE_HD int plane_lines_per_unit(int Np, int nbuf, int nlines_total, int team_siz
 // factors of kPackUnroll elements before any store (a store could alias
 // post, so the compiler would not hoist the next load above it).
 template <typename W, bool BACK>
-FDE_D void rows_from_sv(W* sv, int nb, int n1, int Np, long long o0, const W* post, W* out) {
+FDE_D void rows_from_sv(const Grp& g, W* sv, int nb, int n1, int Np, long long o0, const W* post, W* out) {
     constexpr int U = kPackUnroll<W>;
     const int total = nb * n1;
-    const int nt = blockDim.x;
-    for (int base = threadIdx.x; base < total; base += U * nt) {
+    const int nt = g.nt;
+    for (int base = g.tid; base < total; base += U * nt) {
         W f[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -680,24 +736,24 @@ template <typename W>
 FDE_NI void plane_dst_rows(const Team& t, const Inst& I, const Wk& wk, Combo<W> u, const W* post, W* out) {
     const AxisData& A = I.ax[0];
     const int n1 = A.n, Np = A.Np, n2 = I.n2;
-    const int B = plane_lines_per_unit<W>(Np, 1, n2, t.size, wk.bytes, 1);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    const PlaneSplit ps = plane_split<W>(t, wk, Np, 1, n2, 1, kRowHalves);
+    const Grp& g = ps.g;
+    const int B = ps.B;
+    cx<W>* buf = reinterpret_cast<cx<W>*>(ps.smem);
     W* sv = reinterpret_cast<W*>(buf + padded_len(B * Np));
-    const int units = (n2 + B - 1) / B;
-    for (int un = t.rank; un < units; un += t.size) {
+    for (int un = ps.first; un < ps.units; un += ps.step) {
         const int row0 = un * B;
         const int nb = (n2 - row0) < B ? (n2 - row0) : B;
-        cta_pack<W, kExtOdd, false>(buf, nb, n1, Np, [&](int l, int k, bool d) {
+        cta_pack<W, kExtOdd, false>(g, buf, nb, n1, Np, [&](int l, int k, bool d) {
             return u.get((long long)(row0 + l) * n1 + (k - 1), d);
         });
         trace_mark(t, 70);
-        fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
-        trace_mark(t, 86);
-        cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
+        fft_dst_lines<W>(g, buf, sv, nb, Np, A.logNp, wk.tw);
         trace_mark(t, 87);
-        rows_from_sv<W, false>(sv, nb, n1, Np, (long long)row0 * n1, post, out);
-        __syncthreads();
+        rows_from_sv<W, false>(g, sv, nb, n1, Np, (long long)row0 * n1, post, out);
+        grp_sync(g);
     }
+    __syncthreads();
 }
 
 // tau^{-1} along columns in place: z[:, c] <- S2 diag(phi) S2 z[:, c].
@@ -705,28 +761,26 @@ template <typename W>
 FDE_NI void plane_tau_cols(const Team& t, const Inst& I, const Wk& wk, W* z) {
     const AxisData& A = I.ax[1];
     const int n2 = A.n, Np = A.Np, n1 = I.n1;
-    const int C = plane_lines_per_unit<W>(Np, 1, n1, t.size, wk.bytes, 0);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
-    const Mult<W> mu = mult_tau2<W>(I);
-    const int units = (n1 + C - 1) / C;
-    for (int un = t.rank; un < units; un += t.size) {
+    const PlaneSplit ps = plane_split<W>(t, wk, Np, 1, n1, 0, kColHalves);
+    const Grp& g = ps.g;
+    const int C = ps.B;
+    cx<W>* buf = reinterpret_cast<cx<W>*>(ps.smem);
+    const Mult<W>& mu = mult_slot<W>(mult_tau2<W>(I));
+    for (int un = ps.first; un < ps.units; un += ps.step) {
         const int c0 = un * C;
         const int nc = (n1 - c0) < C ? (n1 - c0) : C;
-        cta_pack<W, kExtOdd, true>(buf, nc, n2, Np, [&](int l, int k, bool) {
+        cta_pack<W, kExtOdd, true>(g, buf, nc, n2, Np, [&](int l, int k, bool) {
             return ldw(z + (long long)(k - 1) * n1 + c0 + l);
         });
         trace_mark(t, 72);
-        fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
-        trace_mark(t, 80);
-        cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [&](int l) { return c0 + l; });
-        trace_mark(t, 81);
-        fft_lines<W, true>(buf, A.logNp, nc, Np, wk.tw);
+        fft_spectral_lines<W>(g, buf, nc, Np, A.logNp, wk.tw, mu, c0, nc);
         trace_mark(t, 82);
-        cta_unpack<W, true, false>(buf, nc, n2, Np, [&](int l, int p, W va, W) {
+        cta_unpack<W, true, false>(g, buf, nc, n2, Np, [&](int l, int p, W va, W) {
             z[(long long)p * n1 + c0 + l] = va;
         });
-        __syncthreads();
+        grp_sync(g);
     }
+    __syncthreads();
 }
 
 // x part of the matvec on the rows of s x; epi(o, a, b).
@@ -735,27 +789,27 @@ FDE_NI void plane_matvec_rows(const Team& t, const Inst& I, const Wk& wk, const 
     const AxisData& A = I.ax[0];
     const int n1 = A.n, Np = A.Np, n2 = I.n2;
     const bool sym = I.symx;
-    const int B = plane_lines_per_unit<W>(Np, sym ? 1 : 2, n2, t.size, wk.bytes, 0);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
-    const Mult<W> mu = mult_matvec<W>(A, sym);
-    const int units = (n2 + B - 1) / B;
-    for (int un = t.rank; un < units; un += t.size) {
+    const PlaneSplit ps = plane_split<W>(t, wk, Np, sym ? 1 : 2, n2, 0, kRowHalves);
+    const Grp& g = ps.g;
+    const int B = ps.B;
+    cx<W>* buf = reinterpret_cast<cx<W>*>(ps.smem);
+    const Mult<W>& mu = mult_slot<W>(mult_matvec<W>(A, sym));
+    for (int un = ps.first; un < ps.units; un += ps.step) {
         const int row0 = un * B;
         const int nb = (n2 - row0) < B ? (n2 - row0) : B;
-        cta_pack<W, kExtZero, false>(buf, nb, n1, Np, [&](int l, int k, bool) {
+        cta_pack<W, kExtZero, false>(g, buf, nb, n1, Np, [&](int l, int k, bool) {
             return s * ldw(x + (long long)(row0 + l) * n1 + (k - 1));
         });
-        fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
-        cta_spectral<W>(buf, nb, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
-        fft_lines<W, true>(buf, A.logNp, sym ? nb : 2 * nb, Np, wk.tw);
+        fft_spectral_lines<W>(g, buf, nb, Np, A.logNp, wk.tw, mu, 0, sym ? nb : 2 * nb);
         auto fe = [&](int l, int p) { return epi.fetch((long long)(row0 + l) * n1 + p); };
         auto pu = [&](int l, int p, W va, W vb, const typename Epi<W>::Ops& r) {
             epi.put((long long)(row0 + l) * n1 + p, va, vb, r);
         };
-        if (sym) cta_unpack2<W, false, false>(buf, nb, n1, Np, fe, pu);
-        else cta_unpack2<W, false, true>(buf, nb, n1, Np, fe, pu);
-        __syncthreads();
+        if (sym) cta_unpack2<W, false, false>(g, buf, nb, n1, Np, fe, pu);
+        else cta_unpack2<W, false, true>(g, buf, nb, n1, Np, fe, pu);
+        grp_sync(g);
     }
+    __syncthreads();
 }
 
 // The second sine transform of the 2D tau solve (rows of tprime, D^{-1}
@@ -767,37 +821,32 @@ FDE_NI void plane_dst_matvec_rows(const Team& t, const Inst& I, const Wk& wk, co
     const int n1 = A.n, Np = A.Np, n2 = I.n2;
     const bool sym = I.symx;
     const int nbuf = sym ? 1 : 2;
-    const int B = plane_lines_per_unit<W>(Np, nbuf, n2, t.size, wk.bytes, 1);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
+    const PlaneSplit ps = plane_split<W>(t, wk, Np, nbuf, n2, 1, kRowHalves);
+    const Grp& g = ps.g;
+    const int B = ps.B;
+    cx<W>* buf = reinterpret_cast<cx<W>*>(ps.smem);
     W* sv = reinterpret_cast<W*>(buf + padded_len(nbuf * B * Np));
     const W* dinv = Prec<W>::dinv(I);
     const bool post = I.has_D && I.order == FDE_ORDER_TAU_D;
-    const Mult<W> mu = mult_matvec<W>(A, sym);
+    const Mult<W>& mu = mult_slot<W>(mult_matvec<W>(A, sym));
     const W c0 = W(I.c0);
     const W* dp = Prec<W>::dp(I);
     const W* dm = Prec<W>::dm(I);
-    const int units = (n2 + B - 1) / B;
-    for (int un = t.rank; un < units; un += t.size) {
+    for (int un = ps.first; un < ps.units; un += ps.step) {
         const int row0 = un * B;
         const int nb = (n2 - row0) < B ? (n2 - row0) : B;
-        cta_pack<W, kExtOdd, false>(buf, nb, n1, Np, [&](int l, int k, bool) {
+        cta_pack<W, kExtOdd, false>(g, buf, nb, n1, Np, [&](int l, int k, bool) {
             return ldw(tprime + (long long)(row0 + l) * n1 + (k - 1));
         });
         trace_mark(t, 74);
-        fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
-        trace_mark(t, 90);
-        cta_dst_extract<W>(buf, sv, nb, Np, A.logNp, wk.tw);
+        fft_dst_lines<W>(g, buf, sv, nb, Np, A.logNp, wk.tw);
         trace_mark(t, 91);
-        rows_from_sv<W, true>(sv, nb, n1, Np, (long long)row0 * n1, post ? dinv : nullptr, z);
-        __syncthreads();
+        rows_from_sv<W, true>(g, sv, nb, n1, Np, (long long)row0 * n1, post ? dinv : nullptr, z);
+        grp_sync(g);
         trace_mark(t, 92);
-        cta_pack<W, kExtZero, false>(buf, nb, n1, Np, [&](int l, int k, bool) { return sv[l * Np + k]; });
+        cta_pack<W, kExtZero, false>(g, buf, nb, n1, Np, [&](int l, int k, bool) { return sv[l * Np + k]; });
         trace_mark(t, 93);
-        fft_lines<W, false>(buf, A.logNp, nb, Np, wk.tw);
-        trace_mark(t, 94);
-        cta_spectral<W>(buf, nb, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
-        trace_mark(t, 95);
-        fft_lines<W, true>(buf, A.logNp, nbuf * nb, Np, wk.tw);
+        fft_spectral_lines<W>(g, buf, nb, Np, A.logNp, wk.tw, mu, 0, nbuf * nb);
         trace_mark(t, 96);
         auto fe = [&](int l, int p) {
             const long long o = (long long)(row0 + l) * n1 + p;
@@ -809,55 +858,44 @@ FDE_NI void plane_dst_matvec_rows(const Team& t, const Inst& I, const Wk& wk, co
             if (!sym) v += d.y * vb;
             tmp[o] = v;
         };
-        if (sym) cta_unpack2<W, false, false>(buf, nb, n1, Np, fe, pu);
-        else cta_unpack2<W, false, true>(buf, nb, n1, Np, fe, pu);
-        __syncthreads();
+        if (sym) cta_unpack2<W, false, false>(g, buf, nb, n1, Np, fe, pu);
+        else cta_unpack2<W, false, true>(g, buf, nb, n1, Np, fe, pu);
+        grp_sync(g);
     }
+    __syncthreads();
 }
 
 // y part: epi(o, a, b) with a, b the T_b and T_b^T (or symmetric) products
 // of the columns of s x.  Column units of C columns; a CTA owns its units'
 // columns.
 template <typename W>
-FDE_HD int plane_cols_per_unit(const Inst& I, int team_size, int bytes) {
-    const bool sym = I.symy;
-    const int Np = I.ax[1].Np;
-    const int cap = max_lines<W>(Np, sym ? 1 : 2, bytes);
-    const int want = (I.n1 + team_size - 1) / team_size;
-    int b = want < cap ? want : cap;
-    return b < 1 ? 1 : b;
-}
-
-template <typename W>
 FDE_NI void plane_matvec_cols(const Team& t, const Inst& I, const Wk& wk, const W* x, W s, Epi<W> epi) {
     const AxisData& A = I.ax[1];
     const int n2 = A.n, Np = A.Np, n1 = I.n1;
     const bool sym = I.symy;
-    const int C = plane_cols_per_unit<W>(I, t.size, wk.bytes);
-    cx<W>* buf = reinterpret_cast<cx<W>*>(wk.smem);
-    const Mult<W> mu = mult_matvec<W>(A, sym);
-    const int units = (n1 + C - 1) / C;
-    for (int un = t.rank; un < units; un += t.size) {
+    const PlaneSplit ps = plane_split<W>(t, wk, Np, sym ? 1 : 2, n1, 0, kColHalves);
+    const Grp& g = ps.g;
+    const int C = ps.B;
+    cx<W>* buf = reinterpret_cast<cx<W>*>(ps.smem);
+    const Mult<W>& mu = mult_slot<W>(mult_matvec<W>(A, sym));
+    for (int un = ps.first; un < ps.units; un += ps.step) {
         const int c0 = un * C;
         const int nc = (n1 - c0) < C ? (n1 - c0) : C;
-        cta_pack<W, kExtZero, true>(buf, nc, n2, Np, [&](int l, int k, bool) {
+        cta_pack<W, kExtZero, true>(g, buf, nc, n2, Np, [&](int l, int k, bool) {
             return s * ldw(x + (long long)(k - 1) * n1 + c0 + l);
         });
         trace_mark(t, 76);
-        fft_lines<W, false>(buf, A.logNp, nc, Np, wk.tw);
-        trace_mark(t, 83);
-        cta_spectral<W>(buf, nc, Np, A.logNp, wk.tw, mu, [](int) { return 0; });
-        trace_mark(t, 84);
-        fft_lines<W, true>(buf, A.logNp, sym ? nc : 2 * nc, Np, wk.tw);
+        fft_spectral_lines<W>(g, buf, nc, Np, A.logNp, wk.tw, mu, 0, sym ? nc : 2 * nc);
         trace_mark(t, 85);
         auto fe = [&](int l, int p) { return epi.fetch((long long)p * n1 + c0 + l); };
         auto pu = [&](int l, int p, W va, W vb, const typename Epi<W>::Ops& r) {
             epi.put((long long)p * n1 + c0 + l, va, vb, r);
         };
-        if (sym) cta_unpack2<W, true, false>(buf, nc, n2, Np, fe, pu);
-        else cta_unpack2<W, true, true>(buf, nc, n2, Np, fe, pu);
-        __syncthreads();
+        if (sym) cta_unpack2<W, true, false>(g, buf, nc, n2, Np, fe, pu);
+        else cta_unpack2<W, true, true>(g, buf, nc, n2, Np, fe, pu);
+        grp_sync(g);
     }
+    __syncthreads();
 }
 
 
@@ -966,8 +1004,10 @@ FDE_D bool op_tau_combo(const Team& t, const Inst& I, int line_mode, Combo<W> u,
             // out += z: z first into zbuf (row-local), then the update of the same rows
             plane_dst_rows<W>(t, I, wk, combo_vec<W>(zbuf, W(1)), post ? dinv : nullptr, zbuf);
             __syncthreads();
-            const int B = plane_lines_per_unit<W>(I.ax[0].Np, 1, I.n2, t.size, wk.bytes, 1);
-            const int units = (I.n2 + B - 1) / B;
+            // the rows this CTA's groups wrote: the units of plane_dst_rows' split
+            const PlaneSplit ps = plane_split<W>(t, wk, I.ax[0].Np, 1, I.n2, 1, kRowHalves);
+            const int B = ps.B;
+            const int units = ps.units;
             const Epi<W> e = epi_a<W>(nullptr, o);
             for (int un = t.rank; un < units; un += t.size) {
                 const long long o0 = (long long)un * B * I.n1;
