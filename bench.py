@@ -589,6 +589,45 @@ def section_march2d(args, device, world, clk_index):
             "e2e_bytes_per_step": N * 8}
 
 
+def kappa_estimate(w: dict) -> float:
+    """kappa(M) of a 1D variable-coefficient system from its symbol: the
+    largest eigenvalue of the Toeplitz part is at most 2^(alpha+1) max d and
+    the smallest at least p_alpha(theta_1) min d, theta_1 = pi/(n+1), with
+    p_alpha(theta) = g(theta) + g(-theta), g(theta) = -e^{-i theta}
+    (1 - e^{i theta})^alpha (Sec. 2.2), d = (d_+ + d_-)/2 and the identity
+    shift nu = h^alpha / dt on both."""
+    import numpy as np
+    n, a = w["n1"], w["alpha"]
+    h = w["length"] / (n + 1)
+    nu = h ** a / w["dt"]
+    d = 0.5 * (np.asarray(w["dp"], dtype=np.float64) + np.asarray(w["dm"], dtype=np.float64))
+    th = math.pi / (n + 1)
+    g = lambda t: -np.exp(-1j * t) * np.power(1.0 - np.exp(1j * t), a)
+    p1 = float(np.real(g(th) + g(-th)))
+    return float((nu + d.max() * 2.0 ** (a + 1)) / (nu + d.min() * p1))
+
+
+# An FP32 product carries an error of about u32 ||M|| ||x||: relative to the
+# smallest eigenmodes that is u32 kappa, and the FP32 inner solves need a
+# growing multiple of the FP64 iteration count once it nears 1e-2 (the
+# march1d section reports the counts per alpha beside this rule's choice).
+U32_KAPPA_LIMIT = 1e-2
+
+
+def precision_by_alpha(ws, paths):
+    """Per alpha of the 1D march: the kappa estimate, u32 kappa, the
+    iterations each precision path took, and the precision the u32 kappa
+    rule picks (FP32 inner solves only while u32 kappa < U32_KAPPA_LIMIT)."""
+    out = {}
+    for w in ws:
+        a = str(w["alpha"])
+        k = kappa_estimate(w)
+        its = {p: paths[p]["per_alpha"][a]["iterations"] for p in ("f64", "f32_ir") if p in paths}
+        out[a] = {"kappa_estimate": k, "u32_kappa": k * 2.0 ** -24, "iterations": its,
+                  "choice": "f32_ir" if k * 2.0 ** -24 < U32_KAPPA_LIMIT else "f64"}
+    return out
+
+
 def section_march1d(args, device, world):
     """The 1D variable-coefficient march (n = 65535, alpha in {1.2, 1.5, 1.8},
     20 implicit-Euler steps, GMRES(30), the three alphas batched in one launch
@@ -635,6 +674,9 @@ def section_march1d(args, device, world):
         nsolves = MARCH_1D_STEPS * len(ws)
         rec = dict(ms_per_march=t, solves_per_s=nsolves / (t * 1e-3), unknown_iters_per_s=n * s["iterations"] /
                    (t * 1e-3), **s, schedule={"ctas": schedule[0], "log_p1": schedule[1]})
+        rec["per_alpha"] = {str(w["alpha"]): {"iterations": sum(st[k]["iterations"] for st in stepper.infos()),
+                                              "outer": sum(st[k]["outer"] for st in stepper.infos())}
+                            for k, w in enumerate(ws)}
         if prec == "f64":
             rec["roofline"] = roofline_alu(flops, t, args.fp64_measured, key=f"march1d:{key}",
                                            units=bytes_ / MARCH_1D_STEPS, launches=MARCH_1D_STEPS)
@@ -645,7 +687,8 @@ def section_march1d(args, device, world):
         finals[key] = [x.cpu().numpy() for x in u]
         for p in plans:
             p.close()
-    return {"workload": f"1d-var-n{n}-3alpha-20steps-gmres30", "unknowns": n, "paths": out, "finals": finals}
+    return {"workload": f"1d-var-n{n}-3alpha-20steps-gmres30", "unknowns": n, "paths": out, "finals": finals,
+            "precision_by_alpha": precision_by_alpha(ws, out)}
 
 
 def section_latency1d(args, device, world):

@@ -164,3 +164,29 @@ def test_algorithmic_byte_count_matches_an_enumeration_of_the_passes():
     assert bench.solve_bytes(info, g, 8) == pytest.approx(passes * 8 * N)
     info32 = dict(info, iterations64=0)
     assert bench.solve_bytes(info32, g, 4) == pytest.approx(passes * 4 * N)
+
+
+def test_kappa_estimate_orders_the_alphas_and_the_rule_splits_them():
+    """The symbol-based kappa(M) estimate grows with alpha on the 1D march
+    (about h^-alpha), and the u32 kappa rule keeps FP32 inner solves for
+    alpha = 1.2 only; against a dense condition number at small n the
+    estimate is an upper bound within two orders."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import oracle
+    import workloads
+    ws = workloads.var_1d_time_stepping(n=65535, alphas=(1.2, 1.5, 1.8), steps=2)
+    ks = [bench.kappa_estimate(w) for w in ws]
+    assert ks[0] < ks[1] < ks[2]
+    fake = {"f64": {"per_alpha": {str(w["alpha"]): {"iterations": 1} for w in ws}}}
+    choice = {a: v["choice"] for a, v in bench.precision_by_alpha(ws, fake).items()}
+    assert choice == {"1.2": "f32_ir", "1.5": "f64", "1.8": "f64"}
+    w = workloads.var_1d_time_stepping(n=255, alphas=(1.5,), steps=2)[0]
+    n = w["n1"]
+    h = w["length"] / (n + 1)
+    prob = oracle.Problem1D(alpha=1.5, n=n, c0=h ** 1.5 / w["dt"], dp=w["dp"], dm=w["dm"])
+    kd = np.linalg.cond(prob.dense())
+    ke = bench.kappa_estimate(w)
+    assert kd <= ke * 1.01 and ke <= 100 * kd, (kd, ke)
