@@ -806,9 +806,11 @@ def section_batch(args, device, rank, world):
             solve()
         torch.cuda.synchronize()
         ms = _timed(solve, device, world, reps=args.side_steps, flush=flush, pre=zero)
-        # assembly + solve: the plans' symbol data rebuilt on the stream first
-        # (the same device kernels fde_assemble_symbol launches)
-        ms_asm = _timed(lambda: ([p.reassemble() for p in plans], solve()), device, world,
+        # assembly + solve: the plans' symbol data rebuilt first (the same device
+        # kernels fde_assemble_symbol launches), the plans spread over side
+        # streams that join the timed stream before the solve launch
+        from paper_1912_13304_gb300.solver import reassemble_all
+        ms_asm = _timed(lambda: (reassemble_all(plans), solve()), device, world,
                         reps=args.side_steps, flush=flush, pre=zero)
         infos = fde.decode_info(info.cpu().numpy().tobytes(), len(ws))
         max_its = {k: 0 for k in BATCH_KS}

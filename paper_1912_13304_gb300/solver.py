@@ -134,6 +134,36 @@ class Plan:
             pass
 
 
+_SIDE_STREAMS: dict = {}
+
+
+def reassemble_all(plans: Sequence[Plan], streams: int = 16) -> None:
+    """Rebuild every plan's symbol data (fde_assemble_symbol again), the plans
+    spread round-robin over `streams` side streams that start after, and
+    join, the current stream.  One plan's assembly kernels are single-CTA
+    jobs, so plans on different streams assemble on different SMs at once
+    instead of one after another."""
+    torch = _torch()
+    if not plans:
+        return
+    dev = torch.cuda.current_device()
+    pool = _SIDE_STREAMS.setdefault(dev, [])
+    k = max(1, min(streams, len(plans)))
+    while len(pool) < k:
+        pool.append(torch.cuda.Stream(device=dev))
+    cur = torch.cuda.current_stream()
+    start = torch.cuda.Event()
+    start.record(cur)
+    for st in pool[:k]:
+        st.wait_event(start)
+    for i, p in enumerate(plans):
+        p.reassemble(stream=pool[i % k])
+    for st in pool[:k]:
+        done = torch.cuda.Event()
+        done.record(st)
+        cur.wait_event(done)
+
+
 def solve_batch(plans: Sequence[Plan], b: Sequence, x: Sequence, tol: float = 1e-8, max_iters: int = 5000,
                 inner_tol: float = 1e-4, max_outer: int = 50, side: str = "right", info_dev=None, stream=None,
                 read_info: bool = True, balance: bool = False):

@@ -196,6 +196,30 @@ def test_batched_case1_instances(gpu):
         assert rel_err(xx, ref.x) < 1e-6
 
 
+def test_reassemble_all_on_side_streams_matches_one_by_one(gpu):
+    """Plans reassembled on side streams at once give the same symbol data as
+    one after another: the batch's solves after each are bit-identical, and
+    the first instance matches the oracle."""
+    from paper_1912_13304_gb300.solver import reassemble_all
+    ws = workloads.const_1d_batch(count=20, kmin=8, kmax=12)
+    plans = [fde.Plan.from_workload(w) for w in ws]
+    bs = [p.c0 * to_dev(gpu, w["b"], "f64") for p, w in zip(plans, ws)]
+    for p in plans:
+        p.reassemble()
+    xs1 = [gpu.zeros_like(b) for b in bs]
+    inf1 = fde.solve_batch(plans, bs, xs1, tol=1e-10)
+    reassemble_all(plans, streams=8)
+    xs2 = [gpu.zeros_like(b) for b in bs]
+    inf2 = fde.solve_batch(plans, bs, xs2, tol=1e-10)
+    for a, b_, x1, x2 in zip(inf1, inf2, xs1, xs2):
+        assert a["status"] == fde.OK and a["iterations"] == b_["iterations"], (a, b_)
+        assert gpu.equal(x1, x2)
+    prob = oracle_problem_1d(ws[0])
+    b0 = prob.c0 * ws[0]["b"]
+    ref = oracle.pcg(prob.matvec, b0, Pinv=oracle.Tau1D.for_problem(prob, shift=True).apply_inverse, tol=1e-13)
+    assert rel_err(xs2[0].cpu().numpy(), ref.x) < 1e-8
+
+
 @pytest.mark.parametrize("precision", ["f64", "f32_ir"])
 @pytest.mark.parametrize("n", [63, 255])
 def test_2d_pcg_shifted(gpu, n, precision):
