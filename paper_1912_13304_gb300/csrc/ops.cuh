@@ -662,8 +662,10 @@ FDE_HD int plane_group_bytes(int bytes, int ng) { return (bytes / ng) & ~255; }
 // Thread groups per CTA of a plane phase: the two halves when a line with
 // its buffers fits half the work area and the FFT's widest pass fits half
 // the threads (FP32 lines up to 4096 points), else the whole CTA.  While one
-// half waits on the global loads of a pack or an epilogue, the other runs
-// its FFT passes; a whole-CTA phase leaves the SM's pipes idle in turn.
+// half waits on the global loads of a pack or an epilogue, the other can run
+// its FFT passes.  Measured on the 4095^2 FP32 plane: the row phase that
+// fuses the second sine transform with the x part of the matvec takes 6 %
+// less time, the other row phases the same.
 template <typename W>
 FDE_HD int plane_groups(int Np, int nbuf, int bytes, int extra_real, int threads) {
     if (fft_lines_per_call(ilog2(Np), threads / 2, (int)sizeof(W)) < 1) return 1;
