@@ -251,11 +251,13 @@ __device__ double symbol_sample(double a, int weights, int j, int Np) {
     return -rho * ((2.0 - a + a * cospi(u)) * cospi(psi) + a * sinpi(u) * sinpi(psi));
 }
 
-__global__ void __launch_bounds__(1024) k_axis(AxisJob J) {
+// Weights w_0..w_{n+1} and the first column of the L-circulant embedding of
+// T, packed into bufA (one CTA: the weights' prefix product is a block scan).
+__device__ void axis_weights_and_column(const AxisJob& J) {
     const int n = J.n, Np = J.Np;
     const int L = 2 * Np;
     {
-        // weights w_0..w_{n+1}: g_k = (-1)^k binom(alpha, k) = f_1 f_2 ... f_k with
+        // g_k = (-1)^k binom(alpha, k) = f_1 f_2 ... f_k with
         // f_i = -(alpha - i + 1) / i, as a parallel prefix product: each thread
         // multiplies the factors of its chunk of k, a block scan gives each
         // thread the product of all earlier chunks, and the thread then forms
@@ -295,36 +297,102 @@ __global__ void __launch_bounds__(1024) k_axis(AxisJob J) {
         }
         J.bufA[m] = mk(c[0], c[1]);
     }
+}
+
+// lambda_j / L from the packed transform Z for the pair (j, Np - j), both
+// precisions.
+__device__ void axis_lambda_pair(const AxisJob& J, const cx<double>* Z, int j) {
+    const int Np = J.Np;
+    const int wsh = J.logTW - (J.logNp + 1);
+    const double invL = 1.0 / (double)(2 * Np);
+    const int jm = (Np - j) & (Np - 1);
+    cx<double> a, b;
+    unpack_pair(Z[j], Z[jm], J.tw64[j << wsh], a, b);
+    const cx<double> la = invL * a, lb = invL * conj(b);
+    J.lam64[j] = la;
+    J.lam32[j] = mk((float)la.x, (float)la.y);
+    J.lam64[Np - j] = lb;
+    J.lam32[Np - j] = mk((float)lb.x, (float)lb.y);
+}
+
+// The tau multiplier (or 2D axis part) at frequency j.
+__device__ void axis_phi(const AxisJob& J, int j) {
+    const int n = J.n, Np = J.Np;
+    const double invL = 1.0 / (double)(2 * Np);
+    double v = 0.0;
+    if (j >= 1 && j <= n) {
+        const double F = symbol_sample(J.alpha, J.weights, j, Np);
+        if (J.kind == 0 && J.dbar) {
+            v = invL / (F + J.add / *J.dbar);
+        } else if (J.kind == 0 && J.fold_d) {
+            const double Dj = 0.5 * ((J.dp ? J.dp[j - 1] : J.dpc) + (J.dm ? J.dm[j - 1] : J.dmc));
+            v = invL / (Dj * F);
+        } else {
+            v = J.kind == 0 ? invL / (J.add + J.mult * F) : J.add + J.mult * F;
+        }
+    }
+    J.phi64[j] = v;
+    J.phi32[j] = (float)v;
+}
+
+// A short axis in one CTA: weights, the ping-pong FFT, lambda and the
+// multiplier samples.
+__global__ void __launch_bounds__(1024) k_axis(AxisJob J) {
+    axis_weights_and_column(J);
     __syncthreads();
     cx<double>* Z = fft_pingpong<double, false>(J.bufA, J.bufB, J.logNp, J.tw64, J.logTW);
-    const int wsh = J.logTW - (J.logNp + 1);
-    const double invL = 1.0 / (double)L;
-    for (int j = threadIdx.x; j <= Np / 2; j += blockDim.x) {
-        const int jm = (Np - j) & (Np - 1);
-        cx<double> a, b;
-        unpack_pair(Z[j], Z[jm], J.tw64[j << wsh], a, b);
-        J.lam64[j] = invL * a;
-        J.lam64[Np - j] = invL * conj(b);
+    for (int j = threadIdx.x; j <= J.Np / 2; j += blockDim.x) axis_lambda_pair(J, Z, j);
+    for (int j = threadIdx.x; j <= J.Np; j += blockDim.x) axis_phi(J, j);
+}
+
+// A long axis across the GPU: the weights in one CTA, then every radix pass of
+// the ping-pong FFT, the lambda pairs and the multiplier samples (one
+// transcendental-heavy FP64 evaluation per frequency) as grid-wide launches.
+// One CTA took 4.4 ms for Np = 65536, most of it in the samples.
+__global__ void __launch_bounds__(1024) k_axis_weights(AxisJob J) { axis_weights_and_column(J); }
+
+template <int RAD>
+__global__ void k_axis_fft_pass(const cx<double>* src, cx<double>* dst, int logP, int logNs, const cx<double>* tw,
+                                int logTW) {
+    constexpr int LR = RAD == 8 ? 3 : (RAD == 4 ? 2 : 1);
+    const int logItems = logP - LR;
+    const int items = 1 << logItems;
+    const int twsh = logTW - logNs - LR;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < items; j += gridDim.x * blockDim.x)
+        stockham_item_pp<double, RAD, false>(src, dst, j, logItems, 1 << logNs, twsh, tw);
+}
+
+__global__ void k_axis_spectrum(AxisJob J, const cx<double>* Z) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= J.Np / 2; j += stride) axis_lambda_pair(J, Z, j);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= J.Np; j += stride) axis_phi(J, j);
+}
+
+// Lines of at least this many packed points take the grid-wide path.
+constexpr int kAxisGridNp = 8192;
+
+void launch_axis(const AxisJob& J, int num_sms, cudaStream_t st) {
+    if (J.Np < kAxisGridNp) {
+        k_axis<<<1, 1024, 0, st>>>(J);
+        return;
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j <= Np; j += blockDim.x) {
-        const cx<double> l = J.lam64[j];
-        J.lam32[j] = mk((float)l.x, (float)l.y);
-        double v = 0.0;
-        if (j >= 1 && j <= n) {
-            const double F = symbol_sample(J.alpha, J.weights, j, Np);
-            if (J.kind == 0 && J.dbar) {
-                v = invL / (F + J.add / *J.dbar);
-            } else if (J.kind == 0 && J.fold_d) {
-                const double Dj = 0.5 * ((J.dp ? J.dp[j - 1] : J.dpc) + (J.dm ? J.dm[j - 1] : J.dmc));
-                v = invL / (Dj * F);
-            } else {
-                v = J.kind == 0 ? invL / (J.add + J.mult * F) : J.add + J.mult * F;
-            }
-        }
-        J.phi64[j] = v;
-        J.phi32[j] = (float)v;
+    k_axis_weights<<<1, 1024, 0, st>>>(J);
+    const int blocks = num_sms > 0 ? num_sms : 1;
+    cx<double>* src = J.bufA;
+    cx<double>* dst = J.bufB;
+    int logNs = 0;
+    for (int rem = J.logNp; rem > 0;) {
+        const int lr = rem >= 3 ? 3 : rem;
+        if (lr == 3) k_axis_fft_pass<8><<<blocks, 256, 0, st>>>(src, dst, J.logNp, logNs, J.tw64, J.logTW);
+        else if (lr == 2) k_axis_fft_pass<4><<<blocks, 256, 0, st>>>(src, dst, J.logNp, logNs, J.tw64, J.logTW);
+        else k_axis_fft_pass<2><<<blocks, 256, 0, st>>>(src, dst, J.logNp, logNs, J.tw64, J.logTW);
+        logNs += lr;
+        rem -= lr;
+        cx<double>* t = src;
+        src = dst;
+        dst = t;
     }
+    k_axis_spectrum<<<blocks, 256, 0, st>>>(J, src);
 }
 
 struct VecJob {
@@ -691,7 +759,7 @@ fde_status fde_assemble_symbol(const fde_problem* prob, const fde_solve_opts* op
         J.wts = at<double>(workspace, Lo.wts);
         J.bufA = at<cx<double>>(workspace, Lo.split64);
         J.bufB = J.bufA + std::max(Lo.Np[0], Lo.Np[1]);
-        k_axis<<<1, 1024, 0, st>>>(J);
+        launch_axis(J, di->num_sms, st);
     }
     VecJob V{};
     V.N = I.N;

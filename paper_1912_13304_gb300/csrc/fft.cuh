@@ -358,6 +358,28 @@ FDE_NI void fft_lines(const Grp g, cx<R>* buf, int logP, int nlines, int lstride
 
 // Ping-pong variant for one long line in global memory (one CTA, symbol
 // assembly only).  Returns the buffer that holds the result.
+// Item j of one ping-pong Stockham pass (the same steps as the shared-memory
+// pass, on global buffers).
+template <typename R, int RAD, bool INV>
+FDE_D void stockham_item_pp(const cx<R>* src, cx<R>* dst, int j, int logItems, int Ns, int twsh, const cx<R>* tw) {
+    const int k = j & (Ns - 1);
+    cx<R> v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[r] = src[j + (r << logItems)];
+    if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+            cx<R> w = tw[(r * k) << twsh];
+            if (INV) w = conj(w);
+            v[r] = v[r] * w;
+        }
+    }
+    dft_reg<R, RAD, INV>(v);
+    const int d = (j - k) * RAD + k;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) dst[d + r * Ns] = v[r];
+}
+
 template <typename R, int RAD, bool INV>
 FDE_D void stockham_pass_pp(const cx<R>* src, cx<R>* dst, int logP, int logNs, const cx<R>* tw,
                             int logTW) {
@@ -366,24 +388,8 @@ FDE_D void stockham_pass_pp(const cx<R>* src, cx<R>* dst, int logP, int logNs, c
     const int items = 1 << logItems;
     const int Ns = 1 << logNs;
     const int twsh = logTW - logNs - LR;
-    for (int j = threadIdx.x; j < items; j += blockDim.x) {
-        const int k = j & (Ns - 1);
-        cx<R> v[RAD];
-#pragma unroll
-        for (int r = 0; r < RAD; ++r) v[r] = src[j + (r << logItems)];
-        if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < RAD; ++r) {
-                cx<R> w = tw[(r * k) << twsh];
-                if (INV) w = conj(w);
-                v[r] = v[r] * w;
-            }
-        }
-        dft_reg<R, RAD, INV>(v);
-        const int d = (j - k) * RAD + k;
-#pragma unroll
-        for (int r = 0; r < RAD; ++r) dst[d + r * Ns] = v[r];
-    }
+    for (int j = threadIdx.x; j < items; j += blockDim.x)
+        stockham_item_pp<R, RAD, INV>(src, dst, j, logItems, Ns, twsh, tw);
     __syncthreads();
 }
 
