@@ -190,3 +190,34 @@ def test_kappa_estimate_orders_the_alphas_and_the_rule_splits_them():
     kd = np.linalg.cond(prob.dense())
     ke = bench.kappa_estimate(w)
     assert kd <= ke * 1.01 and ke <= 100 * kd, (kd, ke)
+
+
+def test_measured_traffic_scales_by_units_and_drops_a_stale_capture(tmp_path, monkeypatch):
+    """roofline.traffic: DRAM bytes per unit of algorithmic bytes from the
+    capture, times the reporting launch's units; None once the sources'
+    hash differs from the capture's, or without a capture."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    h = bench.source_hash()
+    tab = {"k:now": {"source_hash": h, "dram_bytes": 30.0, "units": 10.0},
+           "k:old": {"source_hash": "0" * 16, "dram_bytes": 30.0, "units": 10.0}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(tab))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_hash", lambda: h)
+    assert bench.measured_traffic("k:now", 7.0) == 21.0
+    assert bench.measured_traffic("k:old", 7.0) is None
+    assert bench.measured_traffic("k:none", 7.0) is None
+
+
+def test_both_arms_name_the_same_headline_config():
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+    a = argparse.Namespace(steps=47, warmup=3)
+    c = bench.headline_config(a)
+    assert c == bench.headline_config(argparse.Namespace(steps=47, warmup=3))
+    assert c["workload"] == "2d-var-n4095-50steps-gmres20" and c["unknowns"] == 4095 * 4095
+    assert c["march"].startswith("steps 4..50 ")
